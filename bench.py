@@ -1,0 +1,378 @@
+"""Benchmark: residual + parameter-gradient collocation points/s on one GB300.
+
+One step = one full pass of the hot path over one batch of collocation points:
+jet forward (all channels, all layers), residual, loss, residual adjoint,
+reverse sweep to the parameter gradient, FP64 reduction and the Adam update
+(jet_train_step).  Default workload: Kuramoto-Sivashinsky, 2->64x5->1 tanh
+MLP, N = 65536 points uniform on [0, 2pi] x [0, 1], plain FP32 form (the
+configuration the points/s metric is quoted on).  Other precision forms of the
+same workload are timed beside it under "forms".
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica of the workload (the
+points are independent; no collective on the data path): weak scaling.
+"""
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "residual+param-grad collocation pts/s on 1 GB300; TC roofline %; rel err vs FP64"
+UNIT = "points/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ks_2x64x5")
+    ap.add_argument("--form", default=None, help="precision form of the headline (default: the workload's)")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def flops_per_point(widths, C):
+    """Algorithmic jet-GEMM flops per point of one step: forward, data gradient
+    and weight gradient of every hidden-to-hidden layer, 2 C w_in w_out each."""
+    f = sum(2.0 * C * widths[l - 1] * widths[l] for l in range(2, len(widths) - 1))
+    return 3.0 * f
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
+    """FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flop x SM clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp64_alu_peak_tflops(sm_mhz=2070.0, sms=152):
+    """FP64 FMA peak: 152 SMs x 2 FP64 lanes per SM partition quad (64 FP64
+    flops/clk/SM on GB300 per unit count ratio 1:64 of FP32) -- reported for
+    context only."""
+    return sms * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ reference
+def run_reference(args, rank, ws):
+    """The oracle (FP64 NumPy) as it stands on the host cores, on a bounded
+    sample of the workload per step."""
+    if rank != 0:
+        return
+    import oracle
+    from oracle import residuals as R
+    from paper_2606_29702_gb300 import workloads as wl
+    spec = wl.WORKLOADS[args.workload]
+    S = 256
+    X = wl.points(spec["domain"], S, spec["seed_pts"])
+    layers = wl.xavier_layers(spec["widths"], spec["seed_par"])
+    fam = R.by_name(spec["family"], **spec["coefs"])
+    src = R.helmholtz_source(X, spec["coefs"]["k"])[:, None] if spec["family"] == "helmholtz" else None
+    theta = wl.pack(layers)
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    for _ in range(args.warmup):
+        oracle.loss_and_grad(fam, wl.unpack(theta, spec["widths"]), X, source=src)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        L, _, g = oracle.loss_and_grad(fam, wl.unpack(theta, spec["widths"]), X, source=src)
+        theta, m, v = oracle.adam_step(theta, m, v, wl.pack(g), k + 1)
+    dt = (time.perf_counter() - t0) / args.steps
+    cores = _blas_threads()
+    val = S / dt
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "points_per_step": S, "widths": spec["widths"],
+                      "note": "FP64 oracle (hyper-dual jets + reverse tape), bounded sample per step"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "%d of the workload's points per step, %d steps" % (S, args.steps)},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def cpu_baseline(spec, seconds):
+    """Oracle points/s on the host cores over a bounded sample (~`seconds` s)."""
+    import oracle
+    from oracle import residuals as R
+    from paper_2606_29702_gb300 import workloads as wl
+    S = 256
+    X = wl.points(spec["domain"], S, spec["seed_pts"] + 7)
+    layers = wl.xavier_layers(spec["widths"], spec["seed_par"])
+    fam = R.by_name(spec["family"], **spec["coefs"])
+    src = R.helmholtz_source(X, spec["coefs"]["k"])[:, None] if spec["family"] == "helmholtz" else None
+    oracle.loss_and_grad(fam, layers, X, source=src)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        oracle.loss_and_grad(fam, layers, X, source=src)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n * S / dt, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
+            "sample": "%d runs of residual+gradient on %d points of the workload (%.1f s)" % (n, S, dt)}
+
+
+# ------------------------------------------------------------------ ours
+def time_form(spec, form, X_host, steps, warmup, flush, want_kernel=False, e2e=False):
+    """Time `steps` train steps of one precision form; returns a dict."""
+    import torch
+    from paper_2606_29702_gb300 import jet, specs
+    from paper_2606_29702_gb300 import workloads as wl
+    sp = specs.by_name(spec["family"], **spec["coefs"])
+    plan = jet.Plan(sp, spec["widths"], form)
+    dt = plan.dtype
+    dev = torch.device("cuda")
+    layers = wl.xavier_layers(spec["widths"], spec["seed_par"])
+    p = torch.tensor(wl.pack(layers), dtype=dt, device=dev)
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    x = torch.tensor(X_host, dtype=dt, device=dev)
+    src = None
+    if sp.has_source:
+        src = torch.tensor(specs.helmholtz_source(X_host, spec["coefs"]["k"]), dtype=dt, device=dev)
+    loss = torch.empty((), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    step = 1
+    for _ in range(warmup):
+        plan.train_step(p, m, v, step, 1e-3, x, src, loss)
+        step += 1
+    torch.cuda.synchronize()
+    if want_kernel:
+        plan.profile(True)
+        plan.profile_read()
+    evs = []
+    for _ in range(steps):
+        flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.train_step(p, m, v, step, 1e-3, x, src, loss)
+        b.record(stream)
+        evs.append((a, b))
+        step += 1
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    out = {"ms_per_step": ms, "value": X_host.shape[0] / (ms * 1e-3), "info": plan.info()}
+    if want_kernel:
+        n, kms = plan.profile_read()
+        plan.profile(False)
+        out["kernel_ms"] = kms / max(n, 1)
+        out["kernel_launches"] = n
+    if e2e:
+        # public API end to end: pinned host X -> device, step, loss -> host
+        xh = torch.tensor(X_host, dtype=dt).pin_memory()
+        lh = torch.empty((), dtype=torch.float64).pin_memory()
+        xd = torch.empty_like(x)
+        evs = []
+        for _ in range(steps):
+            flush()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            xd.copy_(xh, non_blocking=True)
+            plan.train_step(p, m, v, step, 1e-3, xd, src, loss)
+            lh.copy_(loss, non_blocking=True)
+            b.record(stream)
+            evs.append((a, b))
+            step += 1
+        torch.cuda.synchronize()
+        ems = sum(a.elapsed_time(b) for a, b in evs) / steps
+        out["e2e"] = {"value": X_host.shape[0] / (ems * 1e-3), "unit": UNIT,
+                      "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+                      "d2h_bytes_per_step": int(lh.numel() * lh.element_size())}
+    plan.close()
+    return out
+
+
+def run_ours(args, rank, ws, local):
+    import torch
+    from paper_2606_29702_gb300 import workloads as wl
+    spec = dict(wl.WORKLOADS[args.workload])
+    form = args.form or spec["precision"]
+    X = wl.points(spec["domain"], spec["N"], spec["seed_pts"] + rank)
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    # warm-up compile / first launch outside the timed region
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    res = time_form(spec, form, X, args.steps, max(args.warmup, 3), flush, want_kernel=True, e2e=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = max_over_ranks(res["ms_per_step"], ws)
+    value = ws * spec["N"] / (ms * 1e-3)
+    C = res["info"]["n_channels"]
+    fpp = flops_per_point(spec["widths"], C)
+    peaks, peak_kind = measured_peaks()
+    kernel_ms = res["kernel_ms"]
+    achieved = fpp * spec["N"] / (kernel_ms * 1e-3) / 1e12
+    if form in ("fp32", "fp64"):
+        peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) if form == "fp32" else \
+            fp64_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "kernel": "fused SIMT jet kernel (%s)" % form, "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x max clock"}
+    else:
+        peak = peaks["bf16_tflops"] * (0.5 if form == "tf32" else 1.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "tcgen05 jet kernel (%s)" % form, "peak_kind": peak_kind}
+    forms = {}
+    if not args.no_forms and rank == 0:
+        for f in ("fp32", "bf16", "tf32", "fp64"):
+            if f == form:
+                continue
+            try:
+                r = time_form(spec, f, X, max(3, args.steps // 2), 3, flush, want_kernel=True)
+                forms[f] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernel_ms": r["kernel_ms"]}
+            except Exception as e:  # a form this build does not provide
+                forms[f] = {"unavailable": str(e).splitlines()[0][:160]}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "tf32": "tf32",
+                                          "bf16x3": "bf16x3"}[form],
+           "data": "synthetic",
+           "config": {"workload": args.workload, "N": spec["N"], "widths": spec["widths"], "form": form,
+                      "channels": C, "l2": "flushed between steps (2x L2 write, outside the per-step events)",
+                      "step": "jet_train_step: forward jets + residual + loss + reverse sweep + FP64 reduce + Adam"},
+           "e2e": res["e2e"], "gpu_launches": 3 * args.steps, "roofline": roof, "clocks": clk,
+           "forms": forms}
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds) if ws == 1 else None
+        print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_ours(args, rank, ws, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * jet.h -- C ABI of libjet: residual-specific partial-jet PINN kernels for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * What the library computes (Sec. 2.2 of "Verified residual-specific explicit
+ * derivative kernels for physics-informed learning and discretized PDE
+ * adjoints"):
+ *
+ *   * a tanh multilayer perceptron u_theta: R^d -> R^n_out (Eq. 1:
+ *     z^l = W^l a^{l-1} + b^l, a^l = tanh(z^l) for the hidden layers, linear
+ *     output layer);
+ *   * the coordinate derivatives d^alpha u_theta that a PDE residual needs,
+ *     propagated layer by layer as a *partial jet*: only the multi-indices of
+ *     the residual plus their lower-order chain are carried (Sec. 2.2,
+ *     "on-demand partial-jet strategy"); every layer applies W^l to all jet
+ *     channels at once with the bias on the value channel only (Eq. 2-3 and
+ *     the "fused GEMM" of Sec. 2.2), and the tanh composes the jet in closed
+ *     form (Eq. 2, Eq. 3 and their higher-order recursion);
+ *   * the residual r_theta(x) = N(u, d_i u, d_ij u, ...) (Sec. 2.2), here a
+ *     sum of monomials of output-jet entries minus an optional source;
+ *   * the loss L = sum_c (1/N) sum_n r_{c,n}^2 and its gradient with respect
+ *     to every parameter (Sec. 3.1.1: reverse-mode differentiation of the
+ *     scalar loss), by a hand-written reverse sweep of the jet program;
+ *   * one full-batch Adam step (Sec. 3.1.1, learning rate 1e-3 in the paper).
+ *
+ * Conventions shared by every call:
+ *   * All device pointers are CUDA device (or managed) memory owned by the
+ *     caller; the library never frees them.  Calls are asynchronous on the
+ *     given stream (0 = legacy default stream) unless stated.
+ *   * Value type: a plan created with JET_FP64 takes and returns double for
+ *     params, X, source, r_out and grad_out; every other precision takes and
+ *     returns float.  Losses are always double.
+ *   * Parameter packing: for l = 1..L, W^l row-major [out][in] followed by
+ *     b^l [out] (Eq. 1 orientation), all layers back to back.
+ *   * Points X: row-major [N][d]; source: row-major [N][n_res]; r_out:
+ *     row-major [N][n_res].
+ *   * Errors: every call returns a jet_status and never aborts; a thread-
+ *     local message is available from jet_last_error().  Shape and spec
+ *     errors are caught by jet_plan_create.
+ */
+#ifndef JET_H_
+#define JET_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jet_plan_s* jet_plan_t;
+typedef struct jet_batch_s* jet_batch_t;
+typedef void* jet_stream_t; /* a cudaStream_t */
+
+typedef enum {
+  JET_OK = 0,
+  JET_ERR_INVALID = 1,     /* bad argument, shape or spec */
+  JET_ERR_NOT_CLOSED = 2,  /* needed multi-indices not downward closed */
+  JET_ERR_UNSUPPORTED = 3, /* valid request outside what this build supports */
+  JET_ERR_OOM = 4,         /* device allocation failed or budget too small */
+  JET_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
+  JET_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+} jet_status;
+
+typedef enum {
+  JET_FP64 = 0,     /* FP64 SIMT kernels */
+  JET_FP32 = 1,     /* plain FP32 SIMT kernels (no tensor cores) */
+  JET_TF32 = 2,     /* tcgen05 kind::tf32 jet GEMMs, FP32 accumulation */
+  JET_BF16 = 3,     /* tcgen05 kind::f16 (bf16) jet GEMMs, FP32 accumulation */
+  JET_BF16X3 = 4    /* as JET_BF16, plus split bf16 hi/lo products on the
+                       highest-order channels */
+} jet_precision;
+
+/* plan flags */
+#define JET_FLAG_AUTO_CLOSE 0x1  /* close `needed` downward instead of failing */
+#define JET_FLAG_STORE 0x2       /* jet_forward_residual keeps the hidden z-jets
+                                    (if they fit the budget) for the next
+                                    jet_backward_params on the same inputs */
+
+/* One derivative channel d^alpha u_out: alpha[i] = order in coordinate i. */
+typedef struct {
+  int32_t out;
+  uint8_t alpha[4];
+} jet_chan;
+
+/* coef * prod_{j < n_fac} d^{fac[j].alpha} u_{fac[j].out} */
+typedef struct {
+  double coef;
+  int32_t n_fac; /* 0..4 */
+  jet_chan fac[4];
+} jet_monomial;
+
+/* r_c = sum_m mono[c][m] - source_c  for c < n_res. */
+typedef struct {
+  int32_t n_res;                   /* 1..4 */
+  const int32_t* n_mono;           /* [n_res] */
+  const jet_monomial* const* mono; /* [n_res][n_mono[c]] */
+  int32_t has_source;              /* 1: calls pass source [N][n_res] */
+} jet_residual_spec;
+
+typedef struct {
+  int32_t d_in, n_out, n_layers;
+  int32_t n_channels;      /* C = 1 + k channels carried per unit */
+  int32_t closure_class;   /* index of the compiled channel set used */
+  char class_name[32];
+  int64_t n_params;
+  int32_t precision;
+  int32_t store_mode;      /* 1 if jet_forward_residual stores z-jets */
+  int64_t store_max_points;
+  int32_t tile_points;     /* points per tile of the fused kernel */
+  int32_t grid_ctas;       /* persistent CTAs per launch */
+  size_t workspace_bytes;  /* device memory the plan owns */
+} jet_plan_info;
+
+/*
+ * Create a plan for one PDE residual on one network shape.
+ *   spec       residual (Sec. 2.2, r = N(u, du, ...)); copied.
+ *   d_in       number of input coordinates (1..3).
+ *   n_layers   number of weight layers L >= 2 (L-1 tanh hidden layers).
+ *   widths     [L+1]: d_in, hidden widths..., n_out (n_out 1..4).  Hidden
+ *              widths must be multiples of 4 and at most 256.
+ *   needed     [n_needed] multi-indices the residual uses (the out field is
+ *              ignored).  They must be downward closed (every alpha' <= alpha
+ *              present, the value included) unless JET_FLAG_AUTO_CLOSE.  The
+ *              plan carries the smallest compiled channel set containing them
+ *              (Sec. 2.2: only the required states and their lower-order
+ *              chain are propagated).
+ *   prec       jet_precision.
+ *   mem_budget_bytes  upper bound on plan-owned device memory for the z-jet
+ *              store (JET_FLAG_STORE); 0 = no store.  The backward pass always
+ *              works in bounded memory by recomputing the jets of each tile
+ *              from its layer inputs.
+ * On success *out owns device workspace until jet_plan_destroy.
+ */
+jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32_t d_in, int32_t n_layers,
+                           const int32_t* widths, int32_t n_needed, const jet_chan* needed,
+                           jet_precision prec, size_t mem_budget_bytes, int32_t flags);
+
+jet_status jet_plan_get_info(jet_plan_t plan, jet_plan_info* info);
+
+/*
+ * Residual and loss (Sec. 2.2 forward partial-jet pass, Eq. 1-3).
+ *   params    device, packed (see top); X device [N][d]; source device
+ *             [N][n_res] or NULL when the spec has none.
+ *   r_out     device [N][n_res] or NULL.
+ *   loss_out  device double scalar or NULL: sum_c (1/N) sum_n r_{c,n}^2.
+ * N may be 0 (loss 0, nothing written to r_out).
+ */
+jet_status jet_forward_residual(jet_plan_t plan, const void* params, const void* X, int64_t N,
+                                const void* source, void* r_out, double* loss_out, jet_stream_t stream);
+
+/*
+ * Gradient of the loss with respect to every parameter (Sec. 3.1.1 reverse
+ * mode of the scalar loss, here a hand-written adjoint of the jet program).
+ *   grad_out  device, packed like params (value type of the plan).
+ *   loss_out  device double or NULL.
+ *   r_out     device [N][n_res] or NULL (the residual of the same pass).
+ * The hidden jets are recomputed tile by tile from the inputs, unless the plan
+ * stores them and the previous jet_forward_residual on this plan used the same
+ * params, X, N and source pointers (the caller must not have changed their
+ * contents in between).
+ */
+jet_status jet_backward_params(jet_plan_t plan, const void* params, const void* X, int64_t N,
+                               const void* source, void* grad_out, void* r_out, double* loss_out,
+                               jet_stream_t stream);
+
+/*
+ * One full-batch Adam step on params in place (Sec. 3.1.1; beta1 0.9,
+ * beta2 0.999, eps 1e-8, bias-corrected with the 1-based `step`).
+ *   adam_m, adam_v  device, packed like params, value type of the plan;
+ *                   zero before step 1.
+ *   loss_out        device double or NULL: the loss BEFORE the update.
+ * Not available for JET_FP64 plans' mixed forms: any precision works.
+ */
+jet_status jet_train_step(jet_plan_t plan, void* params, void* adam_m, void* adam_v, int64_t step, float lr,
+                          const void* X, int64_t N, const void* source, double* loss_out, jet_stream_t stream);
+
+jet_status jet_plan_destroy(jet_plan_t plan);
+
+/*
+ * Batched ensemble: n independent plans (same precision; any shapes and
+ * residuals) run as ONE persistent launch over a work list of
+ * (instance, chunk of point tiles) items.  Arrays are host arrays of n
+ * device pointers / sizes.
+ */
+jet_status jet_batch_create(jet_batch_t* out, int32_t n, const jet_plan_t* plans, int32_t flags);
+jet_status jet_batch_backward(jet_batch_t batch, const void* const* params, const void* const* X,
+                              const int64_t* N, const void* const* source, void* const* grad_out,
+                              double* loss_out /* device [n] or NULL */, jet_stream_t stream);
+jet_status jet_batch_train_step(jet_batch_t batch, void* const* params, void* const* adam_m,
+                                void* const* adam_v, int64_t step, float lr, const void* const* X,
+                                const int64_t* N, const void* const* source,
+                                double* loss_out /* device [n] or NULL */, jet_stream_t stream);
+jet_status jet_batch_destroy(jet_batch_t batch);
+
+/*
+ * Verification hook for the transpose inner-product test of Eq. 15: applies
+ * the plan's activation-jet rule elementwise in FP64 to n jets of C channels
+ * (layout [n][C]):
+ *   kind 0: out = compose(z)                 (a-jet of z, Eq. 2-3)
+ *   kind 1: out = (d compose / dz)(z) v      (tangent)
+ *   kind 2: out = (d compose / dz)(z)^T v    (adjoint used by the backward)
+ * z, v, out: device double arrays.
+ */
+jet_status jet_debug_activation(jet_plan_t plan, int32_t kind, int64_t n, const double* z, const double* v,
+                                double* out, jet_stream_t stream);
+
+/*
+ * Measurement hook.  While enabled, every call on the plan records a pair of
+ * CUDA events on the call's stream around its dominant kernel (the fused jet
+ * kernel).  jet_plan_profile_read synchronises on those events, returns the
+ * number of recorded launches and their summed device time in milliseconds,
+ * and clears the record.  Enabling costs two event records per call.
+ */
+jet_status jet_plan_profile(jet_plan_t plan, int32_t enable);
+jet_status jet_plan_profile_read(jet_plan_t plan, int64_t* launches, double* total_ms);
+
+/* Thread-local message for the last failing call on this thread. */
+const char* jet_last_error(void);
+
+/* Library version string. */
+const char* jet_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JET_H_ */

@@ -1,0 +1,203 @@
+"""Generate the per-closure jet algebra of the CUDA path (jet_closures_gen.h).
+
+A *closure class* is a downward-closed set of multi-indices (the partial jet
+of Sec. 2.2: the derivative states a residual needs plus the lower-order chain
+that produces them).  For each class this script emits straight-line device
+code, specialised at compile time, for
+
+* ``compose``: the activation rule of the jet, a_alpha = sum over set
+  partitions pi of alpha of phi^(|pi|)(z) prod_{B in pi} z_B -- the
+  multivariate Faa di Bruno formula, of which Eq. 2 (first order) and Eq. 3
+  (second order) are the first two cases and the higher orders follow
+  recursively as Sec. 2.2 states;
+* ``tangent``: its Jacobian-vector product da = (da/dz) v;
+* ``adjoint``: its vector-Jacobian product zb = (da/dz)^T ab, the reverse
+  sweep through the activation used by the parameter gradient.
+
+phi = tanh, with p[k] = phi^(k)(z_0) supplied by ``tanh_derivs``.
+
+Run: python gen_closures.py <out.h>   (the build does this).
+"""
+
+import itertools
+import sys
+from collections import OrderedDict
+
+# name -> (d, list of multi-indices); channel 0 is the value, channels are
+# sorted by total order so the highest-order channels form the last block.
+CLASSES = OrderedDict()
+
+
+def _full(d, order):
+    out = []
+    for n in range(order + 1):
+        for al in itertools.product(range(n + 1), repeat=d):
+            if sum(al) == n:
+                out.append(al)
+    return out
+
+
+def _sort(chans):
+    return sorted(set(tuple(c) for c in chans), key=lambda a: (sum(a), tuple(-x for x in a)))
+
+
+CLASSES["d1o4"] = (1, _sort([(k,) for k in range(5)]))
+CLASSES["xt_burgers"] = (2, _sort([(0, 0), (1, 0), (0, 1), (2, 0)]))
+CLASSES["xt_ks"] = (2, _sort([(0, 0), (1, 0), (0, 1), (2, 0), (3, 0), (4, 0)]))
+CLASSES["d2o2"] = (2, _sort(_full(2, 2)))
+CLASSES["xyz_lap"] = (3, _sort([(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2)]))
+CLASSES["d3o2"] = (3, _sort(_full(3, 2)))
+CLASSES["xyt_ns3"] = (3, _sort([(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (1, 1, 0), (0, 2, 0),
+                                (1, 0, 1), (0, 1, 1), (3, 0, 0), (2, 1, 0), (1, 2, 0), (0, 3, 0)]))
+
+
+def set_partitions(items):
+    if not items:
+        yield []
+        return
+    first, rest = items[0], items[1:]
+    for part in set_partitions(rest):
+        yield [[first]] + part
+        for i in range(len(part)):
+            yield part[:i] + [[first] + part[i]] + part[i + 1:]
+
+
+def fdb_terms(alpha, index):
+    """Faa di Bruno terms of channel alpha: list of (coef, k, [block channel indices])."""
+    d = len(alpha)
+    coords = []
+    for i, k in enumerate(alpha):
+        coords += [i] * k
+    acc = OrderedDict()
+    for part in set_partitions(list(range(len(coords)))):
+        blocks = []
+        for blk in part:
+            b = [0] * d
+            for pos in blk:
+                b[coords[pos]] += 1
+            blocks.append(index[tuple(b)])
+        key = (len(blocks), tuple(sorted(blocks)))
+        acc[key] = acc.get(key, 0) + 1
+    return [(c, k, list(bl)) for (k, bl), c in acc.items()]
+
+
+def jacobian(chans):
+    """J[a][b] = list of monomials (coef, pk, [z indices]) of d a_alpha / d z_beta."""
+    index = {c: i for i, c in enumerate(chans)}
+    C = len(chans)
+    J = [[[] for _ in range(C)] for _ in range(C)]
+    terms = {}
+    for ai, al in enumerate(chans):
+        if sum(al) == 0:
+            terms[ai] = [(1, 0, [])]
+        else:
+            terms[ai] = fdb_terms(al, index)
+        for coef, k, blocks in terms[ai]:
+            # d/dz_0 acts through phi^(k)(z_0)
+            J[ai][0].append((coef, k + 1, list(blocks)))
+            for pos, b in enumerate(blocks):
+                J[ai][b].append((coef, k, blocks[:pos] + blocks[pos + 1:]))
+    # merge equal monomials (same phi order, same multiset of z factors)
+    for ai in range(C):
+        for bi in range(C):
+            acc = OrderedDict()
+            for coef, k, zs in J[ai][bi]:
+                key = (k, tuple(sorted(zs)))
+                acc[key] = acc.get(key, 0) + coef
+            J[ai][bi] = [(c, k, list(zs)) for (k, zs), c in acc.items()]
+    return terms, J
+
+
+def mono(coef, k, zs, zname="z"):
+    parts = ["p[%d]" % k] + ["%s[%d]" % (zname, i) for i in zs]
+    s = "*".join(parts)
+    if coef != 1:
+        s = "T(%d)*%s" % (coef, s)
+    return s
+
+
+def emit_class(name, d, chans):
+    C = len(chans)
+    maxord = max(sum(c) for c in chans)
+    terms, J = jacobian(chans)
+    L = []
+    L.append("struct Cls_%s {" % name)
+    L.append("  static constexpr int D = %d;" % d)
+    L.append("  static constexpr int C = %d;" % C)
+    L.append("  static constexpr int MAXORD = %d;" % maxord)
+    L.append("  static constexpr int NP = %d;  // p[0..MAXORD+1]" % (maxord + 2))
+    first = []
+    for i in range(d):
+        e = tuple(int(j == i) for j in range(d))
+        first.append(chans.index(e) if e in chans else -1)
+    L.append("  // channel index of the first-order channel e_i (-1 if absent)")
+    sel = " ".join("i == %d ? %d :" % (i, f) for i, f in enumerate(first)) + " -1"
+    L.append("  static __host__ __device__ constexpr int first_order(int i) { return %s; }" % sel)
+    L.append("  // first channel index of the highest derivative order")
+    top = min(i for i, c in enumerate(chans) if sum(c) == maxord)
+    L.append("  static constexpr int TOP_BEGIN = %d;" % top)
+    # compose
+    L.append("  template <class T> static __device__ __forceinline__ void compose(const T* z, const T* p, T* a) {")
+    for ai in range(C):
+        expr = " + ".join(mono(c, k, bl) for c, k, bl in terms[ai])
+        L.append("    a[%d] = %s;" % (ai, expr))
+    L.append("  }")
+    # tangent
+    L.append("  template <class T> static __device__ __forceinline__ void tangent(const T* z, const T* p, const T* v, T* da) {")
+    for ai in range(C):
+        parts = []
+        for bi in range(C):
+            if J[ai][bi]:
+                parts.append("(%s)*v[%d]" % (" + ".join(mono(c, k, zs) for c, k, zs in J[ai][bi]), bi))
+        L.append("    da[%d] = %s;" % (ai, " + ".join(parts)))
+    L.append("  }")
+    # adjoint
+    L.append("  template <class T> static __device__ __forceinline__ void adjoint(const T* z, const T* p, const T* ab, T* zb) {")
+    for bi in range(C):
+        parts = []
+        for ai in range(C):
+            if J[ai][bi]:
+                parts.append("ab[%d]*(%s)" % (ai, " + ".join(mono(c, k, zs) for c, k, zs in J[ai][bi])))
+        L.append("    zb[%d] = %s;" % (bi, " + ".join(parts) if parts else "T(0)"))
+    L.append("  }")
+    L.append("};")
+    return "\n".join(L)
+
+
+def emit(path):
+    out = []
+    out.append("// Generated by gen_closures.py -- do not edit.")
+    out.append("// Per-closure jet algebra: Faa di Bruno activation composition (Eq. 2-3 and")
+    out.append("// their higher-order recursion, Sec. 2.2), its tangent and its adjoint.")
+    out.append("#pragma once")
+    out.append("")
+    out.append("namespace jet {")
+    out.append("")
+    for name, (d, chans) in CLASSES.items():
+        out.append("// %s: d=%d, channels %s" % (name, d, " ".join("".join(str(x) for x in c) for c in chans)))
+        out.append(emit_class(name, d, chans))
+        out.append("")
+    # host table
+    out.append("struct ClassInfo { const char* name; int d; int C; int maxord; unsigned char alpha[16][3]; };")
+    out.append("static const ClassInfo kClassInfo[] = {")
+    for name, (d, chans) in CLASSES.items():
+        al = ", ".join("{%s}" % ", ".join(str(c[i]) if i < d else "0" for i in range(3)) for c in chans)
+        out.append("  {\"%s\", %d, %d, %d, {%s}}," % (name, d, len(chans), max(sum(c) for c in chans), al))
+    out.append("};")
+    out.append("static constexpr int kNumClasses = %d;" % len(CLASSES))
+    out.append("")
+    out.append("template <int ID> struct ClassById;")
+    for i, n in enumerate(CLASSES):
+        out.append("template <> struct ClassById<%d> { using type = Cls_%s; };" % (i, n))
+    out.append("")
+    out.append("// X-macro over the classes: JET_FOR_EACH_CLASS(M) expands M(id, Cls_name)")
+    out.append("#define JET_FOR_EACH_CLASS(M) \\")
+    out.append(" \\\n".join("  M(%d, Cls_%s)" % (i, n) for i, n in enumerate(CLASSES)))
+    out.append("")
+    out.append("}  // namespace jet")
+    with open(path, "w") as f:
+        f.write("\n".join(out) + "\n")
+
+
+if __name__ == "__main__":
+    emit(sys.argv[1] if len(sys.argv) > 1 else "jet_closures_gen.h")

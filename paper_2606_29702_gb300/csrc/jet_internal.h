@@ -1,0 +1,107 @@
+// Internal structures shared by the host orchestration (jet_api.cu) and the
+// kernels.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace jet {
+
+constexpr int kMaxLayers = 16;   // weight layers
+constexpr int kMaxTerms = 32;    // residual monomials over all components
+constexpr int kMaxRes = 4;
+constexpr int kMaxOut = 4;
+constexpr int kMaxC = 16;
+
+// One residual monomial: coef * prod fac, fac = o * C + channel index.
+struct DevTerm {
+  double coef;
+  int comp;
+  int nfac;
+  int fac[4];
+};
+
+// Kernel modes
+enum : int {
+  MODE_FWD = 0,        // residual + loss (+ z-jet store when store != null)
+  MODE_FWD_BWD = 1,    // residual + loss + gradient, hidden jets recomputed per tile
+  MODE_BWD_STORE = 2,  // gradient from a z-jet store written by MODE_FWD
+};
+
+// Everything a kernel needs to know about one PINN instance for one call.
+struct DevInstance {
+  int L;               // weight layers
+  int d, n_out, n_res;
+  int widths[kMaxLayers + 1];
+  long long off_W[kMaxLayers];  // offsets (elements) into the packed params
+  long long off_b[kMaxLayers];
+  long long n_params;
+  const void* params;  // packed, value type T
+  const void* Wt;      // packed transposed weights (plan workspace), value type T
+  const void* X;       // [N][d]
+  const void* source;  // [N][n_res] or null
+  void* r_out;         // [N][n_res] or null
+  long long N;
+  double inv_N;
+  int n_terms;
+  DevTerm terms[kMaxTerms];
+  // tiling
+  int P;               // points per tile
+  int pitch;           // smem row pitch (elements) of a jet buffer, >= C * P
+  long long n_tiles;
+  int tiles_per_chunk;
+  int n_chunks;
+  int chunk_base;      // first work-item index of this instance
+  // outputs of the chunk reduction (FP64): [n_chunks][n_params], [n_chunks]
+  double* grad_slices;
+  double* loss_slices;
+  // z-jet store for MODE_FWD / MODE_BWD_STORE: per tile, per hidden layer,
+  // [C * P][w] (unit fastest); null if not stored
+  void* store;
+  long long store_tile_stride;  // elements per tile
+};
+
+// Per-launch arguments of the fused SIMT kernel.
+struct SimtArgs {
+  int mode;
+  int n_inst;
+  const DevInstance* insts;   // device array (batched) or null
+  DevInstance inst0;          // single-instance launches pass it by value
+  int n_items;                // total work items (instance, chunk)
+  const int* item_inst;       // [n_items] instance of each item (batched) or null
+  void* scratch;              // per-CTA z-jet scratch
+  long long scratch_stride;   // elements per CTA slot
+};
+
+constexpr int kSimtThreads = 256;
+
+
+// Reductions and elementwise kernels (jet_reduce.cu)
+// One reduction job per instance: grad[p] = sum_c slices[c][p] in FP64 (fixed
+// order), loss = inv_N * sum_c loss_slices[c]; optionally fused with Adam.
+struct ReduceJob {
+  const double* grad_slices;
+  const double* loss_slices;
+  int n_chunks;
+  long long n_params;
+  double inv_N;
+  void* grad_out;     // value type T or null
+  double* loss_out;   // or null
+  void* params;       // Adam: updated in place (value type T)
+  void* m;
+  void* v;
+};
+cudaError_t launch_transpose_weights(const DevInstance& in, bool fp64, void* Wt, cudaStream_t s);
+// jobs: host array copied by value when n == 1, else a device array
+cudaError_t launch_reduce(const ReduceJob* dev_jobs, const ReduceJob& job0, int n, long long max_params, bool fp64,
+                          bool adam, long long step, float lr, cudaStream_t s);
+
+}  // namespace jet
+
+namespace jet {
+// Per-class entry points, one explicit specialisation per instantiation unit.
+template <int ID> cudaError_t simt_launch_id(bool fp64, const SimtArgs& a, int grid, size_t smem, cudaStream_t s);
+template <int ID> cudaError_t simt_max_active_id(bool fp64, size_t smem, int* blocks);
+template <int ID> cudaError_t debug_activation_id(int kind, long long n, const double* z, const double* v,
+                                                  double* out, cudaStream_t s);
+}  // namespace jet

@@ -1,0 +1,543 @@
+// Fused SIMT partial-jet kernel (FP64 and plain FP32 forms).
+//
+// One persistent launch walks a list of work items (instance, chunk of point
+// tiles).  For every tile of P collocation points a CTA runs, on chip:
+//
+//   forward   layer 1 seed (z^1_0 = W^1 x + b^1, z^1_{e_i} = W^1[:, i], higher
+//             channels 0), then for every hidden layer the jet GEMM
+//             Z^l = W^l A^{l-1} over all C channels with the bias on the value
+//             channel only (Eq. 1-3, Sec. 2.2 "fused GEMM"), and the closed-
+//             form tanh jet composition in registers (Eq. 2-3 recursion);
+//   output    linear output layer on every channel, residual monomials,
+//             loss partial (FP64);
+//   backward  residual adjoint ub = (2 r / N) dr/du, output-layer adjoint,
+//             then for l = L-1 .. 1: activation-jet adjoint (transpose of the
+//             composition), weight gradient sum_cols Zb A^T, bias gradient on
+//             the value channel, data gradient W^T Zb.
+//
+// Jets live in shared memory as [unit][channel-major column] rows:
+// column = alpha * P + n.  A thread owns one unit and TP consecutive points of
+// every channel, so the composition and its adjoint are thread-local.  The
+// hidden z-jets of a tile are written to a per-CTA global scratch slot (or to
+// a full-size store) in the forward and read back in the backward: the
+// memory of the backward is bounded by the number of CTAs, not by N.
+// Gradient partial sums go to a per-(instance, chunk) FP64 slice that exactly
+// one CTA updates, so the final FP64 reduction is deterministic.
+#pragma once
+
+#include "jet_closures_gen.h"
+#include "jet_internal.h"
+
+namespace jet {
+
+template <class T> struct Vec;
+template <> struct Vec<float> { static constexpr int N = 4; using type = float4; };
+template <> struct Vec<double> { static constexpr int N = 2; using type = double2; };
+
+template <class T> __device__ __forceinline__ T dev_tanh(T z);
+template <> __device__ __forceinline__ float dev_tanh<float>(float z) { return tanhf(z); }
+template <> __device__ __forceinline__ double dev_tanh<double>(double z) { return tanh(z); }
+
+// p[k] = tanh^(k)(z) for k < NP, as polynomials of a = tanh z and s = 1 - a^2.
+template <class T, int NP>
+__device__ __forceinline__ void tanh_derivs(T z, T* p) {
+  const T a = dev_tanh<T>(z);
+  const T a2 = a * a;
+  const T s = T(1) - a2;
+  p[0] = a;
+  if (NP > 1) p[1] = s;
+  if (NP > 2) p[2] = T(-2) * a * s;
+  if (NP > 3) p[3] = s * (T(6) * a2 - T(2));
+  if (NP > 4) p[4] = T(8) * a * s * (T(2) - T(3) * a2);
+  if (NP > 5) p[5] = T(8) * s * (T(15) * a2 * a2 - T(15) * a2 + T(2));
+}
+
+template <class T>
+__device__ __forceinline__ void vload(const T* p, T* out) {
+  using V = typename Vec<T>::type;
+  V v = *reinterpret_cast<const V*>(p);
+  const T* q = reinterpret_cast<const T*>(&v);
+#pragma unroll
+  for (int j = 0; j < Vec<T>::N; ++j) out[j] = q[j];
+}
+
+template <class T>
+__device__ __forceinline__ void vstore(T* p, const T* in) {
+  using V = typename Vec<T>::type;
+  V v;
+  T* q = reinterpret_cast<T*>(&v);
+#pragma unroll
+  for (int j = 0; j < Vec<T>::N; ++j) q[j] = in[j];
+  *reinterpret_cast<V*>(p) = v;
+}
+
+struct SimtSmem {
+  int P, pitch, wmax, C, nout, d;
+  __device__ size_t buf_elems() const { return (size_t)wmax * pitch; }
+};
+
+template <class Cls, class T>
+struct SimtTile {
+  static constexpr int C = Cls::C;
+  static constexpr int NP = Cls::NP;
+  static constexpr int TP = Vec<T>::N;
+  static constexpr int NT = kSimtThreads;
+
+  const DevInstance& I;
+  const SimtArgs& A;
+  T* B[3];   // jet buffers [wmax][pitch]
+  T* UO;     // output jets [n_out*C][P]
+  T* UB;     // output adjoints [n_out*C][P]
+  T* XS;     // tile points [P][d]
+  double* RED;
+  int P, pitch;
+  const T* params;
+  const T* Wt;
+
+  __device__ SimtTile(const DevInstance& I_, const SimtArgs& A_, unsigned char* smem) : I(I_), A(A_) {
+    P = I.P;
+    pitch = I.pitch;
+    int wmax = 0;
+    for (int l = 1; l < I.L; ++l) wmax = max(wmax, I.widths[l]);
+    T* base = reinterpret_cast<T*>(smem);
+    size_t be = (size_t)wmax * pitch;
+    B[0] = base;
+    B[1] = base + be;
+    B[2] = base + 2 * be;
+    UO = base + 3 * be;
+    UB = UO + (size_t)I.n_out * C * P;
+    XS = UB + (size_t)I.n_out * C * P;
+    size_t off = (size_t)(XS - base) + (size_t)P * I.d;
+    off = (off * sizeof(T) + 15) / 16 * 16;
+    RED = reinterpret_cast<double*>(smem + off);
+    params = reinterpret_cast<const T*>(I.params);
+    Wt = reinterpret_cast<const T*>(I.Wt);
+  }
+
+  __device__ const T* W(int l) const { return params + I.off_W[l - 1]; }   // l = 1..L
+  __device__ const T* bias(int l) const { return params + I.off_b[l - 1]; }
+  __device__ const T* WtL(int l) const { return Wt + I.off_W[l - 1]; }
+
+  // hidden layer z-jet location for tile t, hidden layer l (1..L-1)
+  __device__ T* zjet(long long tile, int l, bool to_store) const {
+    long long off = 0;
+    for (int k = 1; k < l; ++k) off += (long long)C * P * I.widths[k];
+    if (to_store) return reinterpret_cast<T*>(I.store) + tile * I.store_tile_stride + off;
+    return reinterpret_cast<T*>(A.scratch) + (long long)blockIdx.x * A.scratch_stride + off;
+  }
+
+  // ---------------------------------------------------------------- forward
+  __device__ void layer1(T* out, T* zdst) {
+    const int w = I.widths[1], d = I.d;
+    const T* W1 = W(1);
+    const T* b1 = bias(1);
+    const int ngrp = P / TP;
+    for (int it = threadIdx.x; it < w * ngrp; it += NT) {
+      const int u = it % w, pg = it / w;
+      T wrow[3];
+      for (int i = 0; i < 3; ++i) wrow[i] = i < d ? W1[u * d + i] : T(0);
+      const T bu = b1[u];
+#pragma unroll
+      for (int j = 0; j < TP; ++j) {
+        const int n = pg * TP + j;
+        T z[C], p[NP], a[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) z[c] = T(0);
+        T v = bu;
+        for (int i = 0; i < d; ++i) v += wrow[i] * XS[n * d + i];
+        z[0] = v;
+#pragma unroll
+        for (int i = 0; i < Cls::D; ++i) {
+          const int fo = Cls::first_order(i);
+          if (fo >= 0) z[fo] = wrow[i];
+        }
+        tanh_derivs<T, NP>(z[0], p);
+        Cls::compose(z, p, a);
+#pragma unroll
+        for (int c = 0; c < C; ++c) out[u * pitch + c * P + n] = a[c];
+        if (zdst) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) zdst[(long long)(c * P + n) * w + u] = z[c];
+        }
+      }
+    }
+  }
+
+  // Z^l = W^l A^{l-1} (+ b on channel 0), then a^l = compose(z^l).
+  __device__ void hidden_fwd(int l, const T* in, T* out, T* zdst) {
+    const int wi = I.widths[l - 1], wo = I.widths[l];
+    const T* Wtl = WtL(l);  // [wi][wo]
+    const T* bl = bias(l);
+    const int ngrp = P / TP;
+    for (int it = threadIdx.x; it < wo * ngrp; it += NT) {
+      const int u = it % wo, pg = it / wo;
+      T acc[C][TP];
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int j = 0; j < TP; ++j) acc[c][j] = T(0);
+      const T* inp = in + pg * TP;
+#pragma unroll 2
+      for (int k = 0; k < wi; ++k) {
+        const T wv = __ldg(Wtl + k * wo + u);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          T v[TP];
+          vload<T>(inp + k * pitch + c * P, v);
+#pragma unroll
+          for (int j = 0; j < TP; ++j) acc[c][j] = fma(wv, v[j], acc[c][j]);
+        }
+      }
+      const T bu = bl[u];
+      T outv[C][TP];
+#pragma unroll
+      for (int j = 0; j < TP; ++j) {
+        T z[C], p[NP], a[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) z[c] = acc[c][j];
+        z[0] += bu;
+        tanh_derivs<T, NP>(z[0], p);
+        Cls::compose(z, p, a);
+#pragma unroll
+        for (int c = 0; c < C; ++c) outv[c][j] = a[c];
+        if (zdst) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) zdst[(long long)(c * P + pg * TP + j) * wo + u] = z[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) vstore<T>(out + u * pitch + c * P + pg * TP, outv[c]);
+    }
+  }
+
+  // a^l = compose(z^l) from a stored z-jet [C*P][w]
+  __device__ void compose_from(int l, const T* zsrc, T* out) {
+    const int w = I.widths[l];
+    const int ngrp = P / TP;
+    for (int it = threadIdx.x; it < w * ngrp; it += NT) {
+      const int u = it % w, pg = it / w;
+      T outv[C][TP];
+#pragma unroll
+      for (int j = 0; j < TP; ++j) {
+        T z[C], p[NP], a[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) z[c] = zsrc[(long long)(c * P + pg * TP + j) * w + u];
+        tanh_derivs<T, NP>(z[0], p);
+        Cls::compose(z, p, a);
+#pragma unroll
+        for (int c = 0; c < C; ++c) outv[c][j] = a[c];
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) vstore<T>(out + u * pitch + c * P + pg * TP, outv[c]);
+    }
+  }
+
+  // u_{o,alpha} = W^L a^{L-1}_alpha (+ b^L on the value channel)
+  __device__ void output_layer(const T* in) {
+    const int L = I.L, wi = I.widths[L - 1], no = I.n_out;
+    const T* WL = W(L);
+    const T* bL = bias(L);
+    const int ncol = C * P;
+    for (int it = threadIdx.x; it < no * ncol; it += NT) {
+      const int o = it / ncol, col = it % ncol;
+      T s = col < P ? bL[o] : T(0);
+      for (int k = 0; k < wi; ++k) s = fma(WL[o * wi + k], in[k * pitch + col], s);
+      UO[o * ncol + col] = s;
+    }
+  }
+
+  // residual r_c = sum terms - source, loss partial, and (if bwd) ub = dL/du.
+  __device__ double residual(long long n0, int nvalid, bool bwd) {
+    const int ncol = C * P;
+    double loss = 0.0;
+    if (bwd)
+      for (int i = threadIdx.x; i < I.n_out * ncol; i += NT) UB[i] = T(0);
+    __syncthreads();
+    const T* src = reinterpret_cast<const T*>(I.source);
+    T* rout = reinterpret_cast<T*>(I.r_out);
+    for (int n = threadIdx.x; n < nvalid; n += NT) {
+      T r[kMaxRes];
+      for (int c = 0; c < I.n_res; ++c) r[c] = src ? -src[(n0 + n) * I.n_res + c] : T(0);
+      for (int m = 0; m < I.n_terms; ++m) {
+        const DevTerm& tm = I.terms[m];
+        T prod = T(tm.coef);
+        for (int f = 0; f < tm.nfac; ++f) prod *= UO[tm.fac[f] * P + n];
+        r[tm.comp] += prod;
+      }
+      for (int c = 0; c < I.n_res; ++c) {
+        if (rout) rout[(n0 + n) * I.n_res + c] = r[c];
+        loss += (double)r[c] * (double)r[c];
+      }
+      if (bwd) {
+        const T two_over_n = T(2.0 * I.inv_N);
+        for (int m = 0; m < I.n_terms; ++m) {
+          const DevTerm& tm = I.terms[m];
+          const T g = two_over_n * r[tm.comp] * T(tm.coef);
+          for (int f = 0; f < tm.nfac; ++f) {
+            T prod = g;
+            for (int h = 0; h < tm.nfac; ++h)
+              if (h != f) prod *= UO[tm.fac[h] * P + n];
+            UB[tm.fac[f] * P + n] += prod;
+          }
+        }
+      }
+    }
+    return loss;
+  }
+
+  // ---------------------------------------------------------------- backward
+  // Abar^{L-1} = W^L^T ub; dW^L = sum_cols ub a^{L-1}^T; db^L = sum_n ub_0
+  __device__ void output_bwd(const T* a_last, T* abar, double* g) {
+    const int L = I.L, wi = I.widths[L - 1], no = I.n_out;
+    const T* WL = W(L);
+    const int ncol = C * P;
+    for (int it = threadIdx.x; it < wi * ncol; it += NT) {
+      const int k = it / ncol, col = it % ncol;
+      T s = T(0);
+      for (int o = 0; o < no; ++o) s = fma(WL[o * wi + k], UB[o * ncol + col], s);
+      abar[k * pitch + col] = s;
+    }
+    for (int it = threadIdx.x; it < no * wi; it += NT) {
+      const int o = it / wi, k = it % wi;
+      T s = T(0);
+      for (int col = 0; col < ncol; ++col) s = fma(UB[o * ncol + col], a_last[k * pitch + col], s);
+      g[I.off_W[L - 1] + o * wi + k] += (double)s;
+    }
+    for (int o = threadIdx.x; o < no; o += NT) {
+      T s = T(0);
+      for (int n = 0; n < P; ++n) s += UB[o * ncol + n];
+      g[I.off_b[L - 1] + o] += (double)s;
+    }
+  }
+
+  // Zbar^l = (d compose / dz)^T Abar^l, per (unit, point), z^l read from zsrc.
+  __device__ void act_adjoint(int l, const T* zsrc, const T* abar, T* zbar) {
+    const int w = I.widths[l];
+    const int ngrp = P / TP;
+    for (int it = threadIdx.x; it < w * ngrp; it += NT) {
+      const int u = it % w, pg = it / w;
+      T abv[C][TP], outv[C][TP];
+#pragma unroll
+      for (int c = 0; c < C; ++c) vload<T>(abar + u * pitch + c * P + pg * TP, abv[c]);
+#pragma unroll
+      for (int j = 0; j < TP; ++j) {
+        T z[C], p[NP], ab[C], zb[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          z[c] = zsrc[(long long)(c * P + pg * TP + j) * w + u];
+          ab[c] = abv[c][j];
+        }
+        tanh_derivs<T, NP>(z[0], p);
+        Cls::adjoint(z, p, ab, zb);
+#pragma unroll
+        for (int c = 0; c < C; ++c) outv[c][j] = zb[c];
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) vstore<T>(zbar + u * pitch + c * P + pg * TP, outv[c]);
+    }
+  }
+
+  // dW^l[u][k] += sum_cols Zbar[u][col] A[k][col]; db^l[u] += sum_n Zbar[u][n]
+  __device__ void wgrad(int l, const T* zbar, const T* aprev, double* g) {
+    const int wo = I.widths[l], wi = I.widths[l - 1];
+    const int ncol = C * P;
+    const int nkb = wi / 4;
+    double* gW = g + I.off_W[l - 1];
+    for (int it = threadIdx.x; it < (wo / 4) * nkb; it += NT) {
+      const int kb = it % nkb, ub = it / nkb;
+      T acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) acc[r][s] = T(0);
+      for (int col = 0; col < ncol; col += TP) {
+        T zv[4][TP], av[4][TP];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) vload<T>(zbar + (ub * 4 + r) * pitch + col, zv[r]);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) vload<T>(aprev + (kb + s * nkb) * pitch + col, av[s]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int j = 0; j < TP; ++j) acc[r][s] = fma(zv[r][j], av[s][j], acc[r][s]);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) gW[(ub * 4 + r) * wi + kb + s * nkb] += (double)acc[r][s];
+    }
+    double* gb = g + I.off_b[l - 1];
+    for (int u = threadIdx.x; u < wo; u += NT) {
+      T s = T(0);
+      for (int n = 0; n < P; n += TP) {
+        T v[TP];
+        vload<T>(zbar + u * pitch + n, v);
+#pragma unroll
+        for (int j = 0; j < TP; ++j) s += v[j];
+      }
+      gb[u] += (double)s;
+    }
+  }
+
+  // Abar^{l-1}[k][col] = sum_u W^l[u][k] Zbar^l[u][col]
+  __device__ void dgrad(int l, const T* zbar, T* abar) {
+    const int wo = I.widths[l], wi = I.widths[l - 1];
+    const T* Wl = W(l);  // [wo][wi]
+    const int ngrp = P / TP;
+    for (int it = threadIdx.x; it < wi * ngrp; it += NT) {
+      const int k = it % wi, pg = it / wi;
+      T acc[C][TP];
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int j = 0; j < TP; ++j) acc[c][j] = T(0);
+      const T* zp = zbar + pg * TP;
+#pragma unroll 2
+      for (int u = 0; u < wo; ++u) {
+        const T wv = __ldg(Wl + u * wi + k);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          T v[TP];
+          vload<T>(zp + u * pitch + c * P, v);
+#pragma unroll
+          for (int j = 0; j < TP; ++j) acc[c][j] = fma(wv, v[j], acc[c][j]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) vstore<T>(abar + k * pitch + c * P + pg * TP, acc[c]);
+    }
+  }
+
+  // dW^1[u][i] += sum_n Zbar_0[u][n] x_i[n] + Zbar_{e_i}[u][n]; db^1[u] += sum_n Zbar_0[u][n]
+  __device__ void layer1_bwd(const T* zbar, double* g) {
+    const int w = I.widths[1], d = I.d;
+    double* gW = g + I.off_W[0];
+    double* gb = g + I.off_b[0];
+    for (int u = threadIdx.x; u < w; u += NT) {
+      T sb = T(0), sw[3] = {T(0), T(0), T(0)};
+      for (int n = 0; n < P; ++n) {
+        const T z0 = zbar[u * pitch + n];
+        sb += z0;
+        for (int i = 0; i < d; ++i) sw[i] = fma(z0, XS[n * d + i], sw[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < Cls::D; ++i) {
+        const int fo = Cls::first_order(i);
+        if (fo >= 0 && i < d)
+          for (int n = 0; n < P; ++n) sw[i] += zbar[u * pitch + fo * P + n];
+      }
+      for (int i = 0; i < d; ++i) gW[u * d + i] += (double)sw[i];
+      gb[u] += (double)sb;
+    }
+  }
+
+  // ---------------------------------------------------------------- driver
+  __device__ double tile(long long t, double* g) {
+    const int mode = A.mode;
+    const long long n0 = t * P;
+    const long long rem = I.N - n0;
+    const int nvalid = rem < (long long)P ? (int)rem : P;
+    const int d = I.d;
+    const T* X = reinterpret_cast<const T*>(I.X);
+    for (int i = threadIdx.x; i < P * d; i += NT) {
+      const int n = i / d;
+      XS[i] = n < nvalid ? X[(n0 + n) * d + (i % d)] : T(0);
+    }
+    __syncthreads();
+    const bool use_store = (mode == MODE_BWD_STORE) || (mode == MODE_FWD && I.store != nullptr);
+    const bool write_z = (mode == MODE_FWD_BWD) || (mode == MODE_FWD && I.store != nullptr);
+    const int L = I.L;
+    int cur = 0;
+    if (mode != MODE_BWD_STORE) {
+      layer1(B[0], write_z ? zjet(t, 1, use_store) : nullptr);
+      for (int l = 2; l <= L - 1; ++l) {
+        __syncthreads();
+        hidden_fwd(l, B[cur], B[cur ^ 1], write_z ? zjet(t, l, use_store) : nullptr);
+        cur ^= 1;
+      }
+    } else {
+      compose_from(L - 1, zjet(t, L - 1, true), B[0]);
+    }
+    __syncthreads();
+    output_layer(B[cur]);
+    __syncthreads();
+    const bool bwd = mode != MODE_FWD;
+    double loss = residual(n0, nvalid, bwd);
+    __syncthreads();
+    if (!bwd) return loss;
+    const int ab = (cur + 1) % 3, zb = (cur + 2) % 3, ap = cur;
+    output_bwd(B[cur], B[ab], g);
+    __syncthreads();
+    const bool from_store = mode == MODE_BWD_STORE;
+    for (int l = L - 1; l >= 1; --l) {
+      act_adjoint(l, zjet(t, l, from_store), B[ab], B[zb]);
+      if (l >= 2) compose_from(l - 1, zjet(t, l - 1, from_store), B[ap]);
+      __syncthreads();
+      if (l >= 2) {
+        wgrad(l, B[zb], B[ap], g);
+        dgrad(l, B[zb], B[ab]);
+      } else {
+        layer1_bwd(B[zb], g);
+      }
+      __syncthreads();
+    }
+    return loss;
+  }
+};
+
+template <class Cls, class T>
+__global__ void __launch_bounds__(kSimtThreads) simt_kernel(const __grid_constant__ SimtArgs args) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  for (int k = blockIdx.x; k < args.n_items; k += gridDim.x) {
+    // batched launches walk a cost-ordered list: position k -> item id, and
+    // item id -> instance (second half of item_inst)
+    const int item = args.item_inst ? args.item_inst[k] : k;
+    const DevInstance& I = args.insts ? args.insts[args.item_inst[args.n_items + item]] : args.inst0;
+    const int chunk = item - I.chunk_base;
+    SimtTile<Cls, T> S(I, args, smem);
+    const bool bwd = args.mode != MODE_FWD;
+    double* g = bwd ? I.grad_slices + (long long)chunk * I.n_params : nullptr;
+    if (bwd)
+      for (long long i = threadIdx.x; i < I.n_params; i += kSimtThreads) g[i] = 0.0;
+    __syncthreads();
+    double loss = 0.0;
+    const long long t0 = (long long)chunk * I.tiles_per_chunk;
+    const long long t1 = (t0 + I.tiles_per_chunk < I.n_tiles) ? t0 + I.tiles_per_chunk : I.n_tiles;
+    for (long long t = t0; t < t1; ++t) {
+      loss += S.tile(t, g);
+      __syncthreads();
+    }
+    // block reduction of the loss partial (fixed order)
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
+    if ((threadIdx.x & 31) == 0) S.RED[threadIdx.x >> 5] = loss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < kSimtThreads / 32; ++w) s += S.RED[w];
+      I.loss_slices[chunk] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Elementwise activation rule on [n][C] FP64 jets (verification hook, Eq. 15).
+template <class Cls>
+__global__ void debug_activation_kernel(int kind, long long n, const double* z, const double* v, double* out) {
+  constexpr int C = Cls::C;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double zz[C], vv[C], oo[C], p[Cls::NP];
+    for (int c = 0; c < C; ++c) {
+      zz[c] = z[i * C + c];
+      vv[c] = v ? v[i * C + c] : 0.0;
+    }
+    tanh_derivs<double, Cls::NP>(zz[0], p);
+    if (kind == 0) Cls::compose(zz, p, oo);
+    else if (kind == 1) Cls::tangent(zz, p, vv, oo);
+    else Cls::adjoint(zz, p, vv, oo);
+    for (int c = 0; c < C; ++c) out[i * C + c] = oo[c];
+  }
+}
+
+}  // namespace jet

@@ -1,0 +1,104 @@
+"""Residual specifications of the PDE families as monomial tables for libjet.
+
+A residual component is sum_m coef_m prod_j d^{alpha_j} u_{o_j} minus an
+optional per-point source (Sec. 2.2: r_theta = N(u, d_i u, d_ij u, ...)).
+Multi-indices are tuples of derivative orders per input coordinate.
+
+Families (coordinates in input order):
+* burgers(nu), inputs (x, t): u_t + u u_x - nu u_xx (Sec. 3.1.1).
+* ks(c1, c2, c4), inputs (x, t): u_t + c1 u u_x + c2 u_xx + c4 u_xxxx
+  (Sec. 3.1.1).
+* allen_cahn(eps, k), inputs (x, t): u_t - eps u_xx + k u^3 - k u.
+* helmholtz(k), inputs (x, y, z): u_xx + u_yy + u_zz + k^2 u - f, f passed as
+  the source column.
+* ns_psi(nu), inputs (x, y, t), outputs (psi, p), u = psi_y, v = -psi_x:
+  the momentum residuals of Eq. 16 with the time derivative,
+  r_u = psi_yt + psi_y psi_xy - psi_x psi_yy + p_x - nu (psi_xxy + psi_yyy),
+  r_v = -psi_xt - psi_y psi_xx + psi_x psi_xy + p_y + nu (psi_xxx + psi_xyy).
+"""
+
+import math
+
+
+class Spec:
+    def __init__(self, name, d_in, n_out, components, has_source=False):
+        self.name = name
+        self.d_in = d_in
+        self.n_out = n_out
+        self.components = components  # [[(coef, [(o, alpha), ...]), ...], ...]
+        self.has_source = has_source
+
+    @property
+    def n_res(self):
+        return len(self.components)
+
+    def needed(self):
+        s = {tuple([0] * self.d_in)}
+        for comp in self.components:
+            for _, facs in comp:
+                for _, al in facs:
+                    s.add(tuple(al))
+        return sorted(s)
+
+    def closure(self):
+        out = set()
+        for al in self.needed():
+            stack = [tuple(al)]
+            while stack:
+                a = stack.pop()
+                if a in out:
+                    continue
+                out.add(a)
+                for i, k in enumerate(a):
+                    if k > 0:
+                        b = list(a)
+                        b[i] -= 1
+                        stack.append(tuple(b))
+        return sorted(out, key=lambda a: (sum(a), a))
+
+
+def burgers(nu):
+    X, T, XX, U = (1, 0), (0, 1), (2, 0), (0, 0)
+    return Spec("burgers", 2, 1, [[(1.0, [(0, T)]), (1.0, [(0, U), (0, X)]), (-nu, [(0, XX)])]])
+
+
+def ks(c1=1.0, c2=1.0, c4=1.0):
+    return Spec("ks", 2, 1, [[(1.0, [(0, (0, 1))]), (c1, [(0, (0, 0)), (0, (1, 0))]),
+                              (c2, [(0, (2, 0))]), (c4, [(0, (4, 0))])]])
+
+
+def allen_cahn(eps=1e-4, k=5.0):
+    U = (0, 0)
+    return Spec("allen_cahn", 2, 1, [[(1.0, [(0, (0, 1))]), (-eps, [(0, (2, 0))]),
+                                      (k, [(0, U), (0, U), (0, U)]), (-k, [(0, U)])]])
+
+
+def helmholtz(k=4.0 * math.pi):
+    return Spec("helmholtz", 3, 1, [[(1.0, [(0, (2, 0, 0))]), (1.0, [(0, (0, 2, 0))]), (1.0, [(0, (0, 0, 2))]),
+                                     (k * k, [(0, (0, 0, 0))])]], has_source=True)
+
+
+def ns_psi(nu=0.01):
+    def a(x=0, y=0, t=0):
+        return (x, y, t)
+    ps, pr = 0, 1
+    ru = [(1.0, [(ps, a(y=1, t=1))]), (1.0, [(ps, a(y=1)), (ps, a(x=1, y=1))]),
+          (-1.0, [(ps, a(x=1)), (ps, a(y=2))]), (1.0, [(pr, a(x=1))]),
+          (-nu, [(ps, a(x=2, y=1))]), (-nu, [(ps, a(y=3))])]
+    rv = [(-1.0, [(ps, a(x=1, t=1))]), (-1.0, [(ps, a(y=1)), (ps, a(x=2))]),
+          (1.0, [(ps, a(x=1)), (ps, a(x=1, y=1))]), (1.0, [(pr, a(y=1))]),
+          (nu, [(ps, a(x=3))]), (nu, [(ps, a(x=1, y=2))])]
+    return Spec("ns_psi", 3, 2, [ru, rv])
+
+
+def by_name(name, **coefs):
+    return {"burgers": burgers, "ks": ks, "allen_cahn": allen_cahn, "helmholtz": helmholtz,
+            "ns_psi": ns_psi}[name](**coefs)
+
+
+def helmholtz_source(X, k=4.0 * math.pi):
+    """Manufactured source f = (k^2 - 3 pi^2) sin(pi x) sin(pi y) sin(pi z) (numpy, float64)."""
+    import numpy as np
+    X = np.asarray(X, dtype=np.float64)
+    pi = math.pi
+    return ((k * k - 3 * pi * pi) * np.sin(pi * X[:, 0]) * np.sin(pi * X[:, 1]) * np.sin(pi * X[:, 2]))[:, None]
