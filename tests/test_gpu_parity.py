@@ -196,10 +196,11 @@ def test_train_step_matches_oracle_adam():
     v = torch.zeros_like(p)
     x = torch.tensor(X, device="cuda")
     th, mm, vv = theta.copy(), np.zeros_like(theta), np.zeros_like(theta)
+    lr = float(np.float32(1e-3))  # the ABI passes the learning rate as a C float
     for step in range(1, 4):
-        loss = plan.train_step(p, m, v, step, 1e-3, x)
+        loss = plan.train_step(p, m, v, step, lr, x)
         L, _, gr = oracle.loss_and_grad(fam, wl.unpack(th, spec["widths"]), X)
-        th, mm, vv = oracle.adam_step(th, mm, vv, wl.pack(gr), step)
+        th, mm, vv = oracle.adam_step(th, mm, vv, wl.pack(gr), step, lr=lr)
         torch.cuda.synchronize()
         assert abs(float(loss) - L) <= 1e-12 * abs(L)
     assert rel_l2(p.cpu().numpy(), th) <= 1e-12
@@ -226,8 +227,9 @@ def test_autograd_function_and_fd():
     x64 = torch.tensor(X, device="cuda")
     rng = np.random.default_rng(3)
     for _ in range(3):
-        d = torch.tensor(rng.standard_normal(p64.numel()), device="cuda")
-        h = 1e-5
+        d = rng.standard_normal(p64.numel())
+        d = torch.tensor(d / np.linalg.norm(d), device="cuda")  # unit direction: truncation O(h^2) ~ 1e-8
+        h = 1e-4
         lp = float(plan64.forward(p64 + h * d, x64, want_r=False)[1])
         lm = float(plan64.forward(p64 - h * d, x64, want_r=False)[1])
         fd = (lp - lm) / (2 * h)
