@@ -215,6 +215,36 @@ jet_status jet_debug_activation(jet_plan_t plan, int32_t kind, int64_t n, const 
 jet_status jet_plan_profile(jet_plan_t plan, int32_t enable);
 jet_status jet_plan_profile_read(jet_plan_t plan, int64_t* launches, double* total_ms);
 
+/*
+ * jet_backward_params without any device allocation (the paper has no
+ * counterpart: this is a deployment convenience of this library).
+ *
+ * For callers that cannot call cudaMalloc -- code recording a CUDA graph
+ * against its own memory pools, runtimes that own every device allocation,
+ * or loops that forbid allocator calls after start-up -- and therefore cannot
+ * create a plan.  It takes the jet_plan_create arguments (JET_FP64 or
+ * JET_FP32 only) together with the jet_backward_params arguments, and keeps
+ * all working memory (transposed weights, per-chunk FP64 gradient slices,
+ * per-CTA jet scratch) in one file-scope device array of 8 MiB that every
+ * GPU loading the library reserves until the process exits.
+ *   params, X, source, grad_out, loss_out: as jet_backward_params (device;
+ *             the caller allocates them); N >= 1.
+ *   scratch_bytes_used: optional host out-param, bytes of the array used.
+ * Shapes whose working set exceeds 8 MiB even with a single chunk of tiles
+ * are rejected with JET_ERR_UNSUPPORTED before any launch.
+ * Set-up: the first call on each device looks up the array's device address
+ * with cudaGetSymbolAddress (that device current); make that first call
+ * before any stream capture.  Every call reuses the same array and leaves its
+ * contents behind; each call writes every part it reads, so nothing has to be
+ * cleared, but calls that overlap on the GPU (two streams, two threads, two
+ * graph replays in flight) race on the array and must be serialised.
+ */
+jet_status jet_backward_params_noalloc(const jet_residual_spec* spec, int32_t d_in, int32_t n_layers,
+                                       const int32_t* widths, int32_t n_needed, const jet_chan* needed,
+                                       jet_precision prec, const void* params, const void* X, int64_t N,
+                                       const void* source, void* grad_out, double* loss_out,
+                                       jet_stream_t stream, size_t* scratch_bytes_used);
+
 /* Thread-local message for the last failing call on this thread. */
 const char* jet_last_error(void);
 

@@ -50,7 +50,7 @@ def build(verbose=False, jobs=None):
                            os.path.join(CSRC, "jet_closures_gen.h")])
     cc = nvcc()
     units = []
-    for name in ("jet_api.cu", "jet_reduce.cu", "jet_tc.cu"):
+    for name in ("jet_api.cu", "jet_reduce.cu", "jet_tc.cu", "jet_noalloc.cu"):
         units.append((os.path.join(CSRC, name), os.path.join(BUILD, name.replace(".cu", ".o")), []))
     for k in range(n_classes()):
         units.append((os.path.join(CSRC, "jet_simt_inst.cu"), os.path.join(BUILD, "jet_simt_%d.o" % k),

@@ -80,6 +80,8 @@ cudaError_t debug_act(int cls, int kind, long long n, const double* z, const dou
 
 }  // namespace
 
+void jet::set_last_error(const char* msg) { g_err = msg; }
+
 struct jet_plan_s {
   int device = 0;
   int d = 0, L = 0, n_out = 0, n_res = 0;

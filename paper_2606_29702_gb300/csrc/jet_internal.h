@@ -99,6 +99,9 @@ cudaError_t launch_reduce(const ReduceJob* dev_jobs, const ReduceJob& job0, int 
 }  // namespace jet
 
 namespace jet {
+// Sets the thread-local message returned by jet_last_error() (jet_api.cu).
+void set_last_error(const char* msg);
+
 // Per-class entry points, one explicit specialisation per instantiation unit.
 template <int ID> cudaError_t simt_launch_id(bool fp64, const SimtArgs& a, int grid, size_t smem, cudaStream_t s);
 template <int ID> cudaError_t simt_max_active_id(bool fp64, size_t smem, int* blocks);

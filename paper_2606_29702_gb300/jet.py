@@ -52,7 +52,8 @@ class JetPlanInfo(ctypes.Structure):
 
 EXPORTS = ["jet_plan_create", "jet_plan_get_info", "jet_forward_residual", "jet_backward_params", "jet_train_step",
            "jet_plan_destroy", "jet_batch_create", "jet_batch_backward", "jet_batch_train_step", "jet_batch_destroy",
-           "jet_debug_activation", "jet_plan_profile", "jet_plan_profile_read", "jet_last_error", "jet_version"]
+           "jet_debug_activation", "jet_plan_profile", "jet_plan_profile_read", "jet_backward_params_noalloc",
+           "jet_last_error", "jet_version"]
 
 _lib = None
 
@@ -81,6 +82,9 @@ def load():
                                        vp, vp]
     L.jet_batch_destroy.argtypes = [vp]
     L.jet_debug_activation.argtypes = [vp, i32, i64, vp, vp, vp, vp]
+    L.jet_backward_params_noalloc.argtypes = [ctypes.POINTER(JetResidualSpec), i32, i32, ctypes.POINTER(i32), i32,
+                                              ctypes.POINTER(JetChan), i32, vp, vp, i64, vp, vp, vp, vp,
+                                              ctypes.POINTER(sz)]
     L.jet_plan_profile.argtypes = [vp, i32]
     L.jet_plan_profile_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
     L.jet_last_error.restype = ctypes.c_char_p
