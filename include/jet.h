@@ -68,7 +68,7 @@ typedef enum {
   JET_TF32 = 2,     /* tcgen05 kind::tf32 jet GEMMs, FP32 accumulation */
   JET_BF16 = 3,     /* tcgen05 kind::f16 (bf16) jet GEMMs, FP32 accumulation */
   JET_BF16X3 = 4    /* as JET_BF16, plus split bf16 hi/lo products on the
-                       highest-order channels */
+                       highest-order channels (hidden width <= 128) */
 } jet_precision;
 
 /* plan flags */

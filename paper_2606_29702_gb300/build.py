@@ -55,6 +55,8 @@ def build(verbose=False, jobs=None):
     for k in range(n_classes()):
         units.append((os.path.join(CSRC, "jet_simt_inst.cu"), os.path.join(BUILD, "jet_simt_%d.o" % k),
                       ["-DJET_CLASS_ID=%d" % k]))
+        units.append((os.path.join(CSRC, "jet_tc_inst.cu"), os.path.join(BUILD, "jet_tc_%d.o" % k),
+                      ["-DJET_CLASS_ID=%d" % k]))
     cmds = [[cc] + ARCH + FLAGS + extra + ["-c", src, "-o", obj] for src, obj, extra in units]
     jobs = jobs or max(1, min(len(cmds), os.cpu_count() or 1))
     failed = []

@@ -15,6 +15,7 @@
 #include "../../include/jet.h"
 #include "jet_closures_gen.h"
 #include "jet_internal.h"
+#include "jet_plan.h"
 #include "jet_tc.h"
 
 using namespace jet;
@@ -82,61 +83,26 @@ cudaError_t debug_act(int cls, int kind, long long n, const double* z, const dou
 
 void jet::set_last_error(const char* msg) { g_err = msg; }
 
-struct jet_plan_s {
-  int device = 0;
-  int d = 0, L = 0, n_out = 0, n_res = 0;
-  std::vector<int> widths;
-  int cls = -1, C = 0;
-  jet_precision prec = JET_FP32;
-  bool fp64 = false;
-  bool tc = false;
-  std::vector<DevTerm> terms;
-  bool has_source = false;
-  long long n_params = 0;
-  std::vector<long long> off_W, off_b;
-  int P = 0, pitch = 0;
-  size_t smem = 0;
-  int grid = 0;
-  size_t elem = 4;
-  // workspace
-  void* Wt = nullptr;
-  double* grad_slices = nullptr;
-  double* loss_slices = nullptr;
-  void* scratch = nullptr;
-  long long scratch_stride = 0;
-  void* store = nullptr;
-  long long store_max_points = 0;
-  long long store_tile_stride = 0;
-  size_t ws_bytes = 0;
-  // identity of the forward call whose jets the store holds
-  bool st_valid = false;
-  const void* st_params = nullptr;
-  const void* st_X = nullptr;
-  const void* st_src = nullptr;
-  long long st_N = -1;
-  // tensor-core path state (jet_tc.cu)
-  TcPlan* tcp = nullptr;
-  // measurement hook: event pairs around the dominant kernel
-  bool profiling = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof;
-};
+void jet::plan_prof_begin(jet_plan_s* p, cudaStream_t s) {
+  if (!p->profiling) return;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, s);
+  p->prof.push_back({a, b});
+}
+
+void jet::plan_prof_end(jet_plan_s* p, cudaStream_t s) {
+  if (!p->profiling || p->prof.empty()) return;
+  cudaEventRecord(p->prof.back().second, s);
+}
 
 // Record an event pair around the dominant kernel of a call when profiling.
 struct ProfScope {
   jet_plan_s* p;
   cudaStream_t s;
-  cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(jet_plan_s* p_, cudaStream_t s_) : p(p_), s(s_) {
-    if (!p->profiling) return;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    cudaEventRecord(a, s);
-  }
-  ~ProfScope() {
-    if (!a) return;
-    cudaEventRecord(b, s);
-    p->prof.push_back({a, b});
-  }
+  ProfScope(jet_plan_s* p_, cudaStream_t s_) : p(p_), s(s_) { jet::plan_prof_begin(p, s); }
+  ~ProfScope() { jet::plan_prof_end(p, s); }
 };
 
 namespace {

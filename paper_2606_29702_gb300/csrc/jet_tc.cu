@@ -1,25 +1,498 @@
-// Tensor-core path (placeholder until the tcgen05 kernels land).
-#include "jet_tc.h"
+// Host side of the tensor-core path: plan set-up (tile size under the shared-
+// memory and TMEM budgets, BF16 weight copies and their TMA tensor maps),
+// per-call weight preparation and launches of the fused tcgen05 kernel.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
 
-jet_status tc_plan_create(jet_plan_s*, jet::TcPlan** out, const cudaDeviceProp&, size_t, int) {
-  *out = nullptr;
-  return JET_ERR_UNSUPPORTED;
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "jet_closures_gen.h"
+#include "jet_internal.h"
+#include "jet_plan.h"
+#include "jet_tc.h"
+#include "jet_tc_kernel.cuh"
+
+using namespace jet;
+
+namespace jet {
+
+template <int ID> cudaError_t tc_launch_id(const TcArgs& a, int grid, size_t smem, cudaStream_t s);
+template <int ID> cudaError_t tc_max_active_id(size_t smem, int* blocks);
+
+struct TcPlan {
+  int w = 0, H = 1, P = 0, cols = 0, cols_pad = 0, top_cols = 0, split3 = 0;
+  int tmem_cols = 0, ctas_per_sm = 1, grid = 0;
+  size_t smem = 0;
+  int o_w, o_wlo, o_a0, o_a1, o_alo0, o_alo1, o_uo, o_ub, o_xs, o_red;
+  int act_bytes = 0, alo_bytes = 0, r0w = 0, r1w = 0;
+  long long scratch_stride = 0;
+  // workspace
+  __nv_bfloat16* Wh = nullptr;   // hidden weights [L-2][w][w]
+  __nv_bfloat16* Wl = nullptr;   // output weights [n_out][w]
+  __nv_bfloat16* Wlo = nullptr;  // low parts [L-2][w][w]
+  double* grad_slices = nullptr;
+  double* loss_slices = nullptr;
+  unsigned char* scratch = nullptr;
+  int* err = nullptr;
+  int* h_err = nullptr;
+  cudaEvent_t err_ev = nullptr;
+  size_t ws_bytes = 0;
+  CUtensorMap wmap, wlmap, wlomap;
+};
+
+struct TcBatch {
+  int dummy;
+};
+
+}  // namespace jet
+
+namespace {
+
+cudaError_t tc_launch(int cls, const TcArgs& a, int grid, size_t smem, cudaStream_t s) {
+  switch (cls) {
+#define CASE(id, cl) \
+  case id:           \
+    return tc_launch_id<id>(a, grid, smem, s);
+    JET_FOR_EACH_CLASS(CASE)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
 }
-void tc_plan_destroy(jet::TcPlan*) {}
-int tc_tile_points(const jet::TcPlan*) { return 0; }
-int tc_grid(const jet::TcPlan*) { return 0; }
-size_t tc_workspace_bytes(const jet::TcPlan*) { return 0; }
-jet_status tc_forward(jet_plan_s*, jet::TcPlan*, const void*, const void*, long long, const void*, void*, double*,
-                      cudaStream_t) { return JET_ERR_UNSUPPORTED; }
-jet_status tc_backward(jet_plan_s*, jet::TcPlan*, const void*, const void*, long long, const void*, void*, void*,
-                       double*, cudaStream_t) { return JET_ERR_UNSUPPORTED; }
-jet_status tc_train_step(jet_plan_s*, jet::TcPlan*, void*, void*, void*, long long, float, const void*, long long,
-                         const void*, double*, cudaStream_t) { return JET_ERR_UNSUPPORTED; }
-jet_status tc_batch_create(const std::vector<jet_plan_s*>&, jet::TcBatch** out) {
-  *out = nullptr;
-  return JET_ERR_UNSUPPORTED;
+
+cudaError_t tc_occupancy(int cls, size_t smem, int* blocks) {
+  switch (cls) {
+#define CASE(id, cl) \
+  case id:           \
+    return tc_max_active_id<id>(smem, blocks);
+    JET_FOR_EACH_CLASS(CASE)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
 }
-void tc_batch_destroy(jet::TcBatch*) {}
-jet_status tc_batch_run(jet::TcBatch*, const std::vector<jet_plan_s*>&, const void* const*, void* const*,
-                        void* const*, long long, float, const void* const*, const int64_t*, const void* const*,
-                        void* const*, double*, bool, cudaStream_t) { return JET_ERR_UNSUPPORTED; }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// bf16 tensor [n2][n1][n0] (n0 contiguous), box (64, box1, 1), 128-byte swizzle
+bool encode(CUtensorMap* m, void* base, cuuint64_t n0, cuuint64_t n1, cuuint64_t n2, cuuint32_t box1, int rank) {
+  EncodeTiledFn fn = encoder();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {n0, n1, n2};
+  cuuint64_t strides[2] = {n0 * 2, n0 * n1 * 2};
+  cuuint32_t box[3] = {64, box1, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// fp32 packed params -> bf16 hidden / output weights (and split low parts)
+struct OffW {
+  long long v[kMaxLayers];
+};
+
+__global__ void tc_prep_kernel_v(const float* params, int L, int w, int n_out, OffW offW, __nv_bfloat16* Wh,
+                                 __nv_bfloat16* Wl, __nv_bfloat16* Wlo, long long nh, long long nl) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nh + nl;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i < nh) {
+      const long long l = i / ((long long)w * w), r = i % ((long long)w * w);
+      const float v = params[offW.v[l + 1] + r];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      Wh[i] = hi;
+      if (Wlo) Wlo[i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    } else {
+      const long long r = i - nh;
+      Wl[r] = __float2bfloat16_rn(params[offW.v[L - 1] + r]);
+    }
+  }
+}
+
+jet_status tfail(jet_status st, const char* msg) {
+  jet::set_last_error(msg);
+  return st;
+}
+
+jet_status tcuda(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  jet::set_last_error(buf);
+  return e == cudaErrorMemoryAllocation ? JET_ERR_OOM : JET_ERR_CUDA;
+}
+
+// shared-memory carve for tile size P; returns total bytes (without the 1 KB alignment slack)
+size_t carve(TcPlan& t, int C, int n_out, int d) {
+  const int R = 128 * t.H;
+  const int nck = std::max(2, t.w / 64);
+  const int ach = (t.cols_pad + 63) / 64;
+  const int lch = t.split3 ? (t.top_cols + 63) / 64 : 0;
+  size_t off = 0;
+  t.o_w = (int)off;
+  off += (size_t)nck * R * 128;
+  t.o_wlo = (int)off;
+  if (t.split3) off += (size_t)nck * R * 128;
+  t.act_bytes = ach * (R / 8) * 1024;
+  t.alo_bytes = lch * (R / 8) * 1024;
+  t.o_a0 = (int)off;
+  off += t.act_bytes;
+  t.o_a1 = (int)off;
+  off += t.act_bytes;
+  t.o_alo0 = (int)off;
+  off += t.alo_bytes;
+  t.o_alo1 = (int)off;
+  off += t.alo_bytes;
+  t.o_uo = (int)off;
+  off += (size_t)n_out * C * t.P * 4;
+  t.o_ub = (int)off;
+  off += (size_t)n_out * C * t.P * 4;
+  t.o_xs = (int)off;
+  off += (size_t)t.P * d * 4;
+  off = (off + 15) / 16 * 16;
+  t.o_red = (int)off;
+  off += 64;
+  return off;
+}
+
+}  // namespace
+
+jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& prop, size_t mem_budget, int flags) {
+  (void)mem_budget;
+  (void)flags;
+  *out = nullptr;
+  if (p->prec == JET_TF32) return tfail(JET_ERR_UNSUPPORTED, "JET_TF32 is not provided by this build");
+  const int L = p->L, w = p->widths[1];
+  for (int l = 1; l < L; ++l)
+    if (p->widths[l] != w) return tfail(JET_ERR_UNSUPPORTED, "tensor-core path needs equal hidden widths");
+  if (w % 32 || w < 32 || w > 256) return tfail(JET_ERR_UNSUPPORTED, "tensor-core path needs hidden width 32..256, multiple of 32");
+  if (!encoder()) return tfail(JET_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+  if (p->prec == JET_BF16X3 && w > 128)
+    return tfail(JET_ERR_UNSUPPORTED, "JET_BF16X3 needs hidden width <= 128 (high and low weights share shared memory)");
+  const int C = p->C, maxord = kClassInfo[p->cls].maxord;
+  int top_begin = 0;
+  for (int c = 0; c < C; ++c) {
+    int o = 0;
+    for (int j = 0; j < 3; ++j) o += kClassInfo[p->cls].alpha[c][j];
+    if (o == maxord) {
+      top_begin = c;
+      break;
+    }
+  }
+  TcPlan* t = new TcPlan();
+  t->w = w;
+  t->H = w > 128 ? 2 : 1;
+  t->split3 = p->prec == JET_BF16X3 ? 1 : 0;
+  const int ntop = C - top_begin;
+  // choose P: most points per SM (P x CTAs per SM), shared memory <= 220 KB,
+  // TMEM <= 512 columns per SM
+  int best_score = -1;
+  TcPlan best = *t;
+  for (int P = 8; P <= 64; P += 8) {
+    TcPlan c = *t;
+    c.P = P;
+    c.cols = C * P;
+    c.cols_pad = (c.cols + 15) / 16 * 16;
+    if (c.cols_pad > 256) break;
+    c.top_cols = ntop * P;
+    if (c.split3 && c.top_cols % 16) continue;
+    const size_t sm = carve(c, C, p->n_out, p->d) + 1024;
+    if (sm > 220 * 1024) continue;
+    const int NB = c.H == 2 ? 128 : w;
+    c.r0w = std::max(c.cols_pad, NB);
+    c.r1w = c.cols_pad;
+    const int need = c.H * (c.r0w + c.r1w);
+    int tm = 32;
+    while (tm < need) tm *= 2;
+    if (tm > 512) continue;
+    c.tmem_cols = tm;
+    const int by_tmem = 512 / tm;
+    const int by_smem = (int)((228 * 1024) / (sm + 1024));
+    c.ctas_per_sm = std::max(1, std::min(by_tmem, by_smem));
+    const int score = P * c.ctas_per_sm;
+    if (score > best_score) {
+      best_score = score;
+      best = c;
+    }
+  }
+  if (best_score < 0) {
+    delete t;
+    return tfail(JET_ERR_UNSUPPORTED, "no tile size fits shared memory and TMEM");
+  }
+  *t = best;
+  // pad the shared-memory request so that no more CTAs share an SM than TMEM allows
+  size_t sm = carve(*t, C, p->n_out, p->d) + 1024;
+  const size_t floor_sm = (228 * 1024) / (t->ctas_per_sm + 1) + 1024;
+  t->smem = std::max(sm, floor_sm);
+  int occ = 0;
+  cudaError_t e = tc_occupancy(p->cls, t->smem, &occ);
+  if (e != cudaSuccess || occ < 1) {
+    delete t;
+    return e != cudaSuccess ? tcuda(e, "tc occupancy") : tfail(JET_ERR_UNSUPPORTED, "tensor-core tile does not fit");
+  }
+  t->ctas_per_sm = std::min(t->ctas_per_sm, occ);
+  t->grid = prop.multiProcessorCount * t->ctas_per_sm;
+  t->scratch_stride = (long long)std::max(0, L - 3) * (t->act_bytes + t->alo_bytes);
+  // workspace
+  const long long nh = (long long)std::max(0, L - 2) * w * w, nl = (long long)p->n_out * w;
+  size_t b_wh = std::max<long long>(nh, 1) * 2, b_wl = nl * 2, b_wlo = t->split3 ? b_wh : 0;
+  size_t b_gs = (size_t)t->grid * p->n_params * 8, b_ls = (size_t)t->grid * 8;
+  size_t b_sc = (size_t)t->grid * std::max<long long>(t->scratch_stride, 16);
+  e = cudaMalloc((void**)&t->Wh, b_wh);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t->Wl, b_wl);
+  if (e == cudaSuccess && t->split3) e = cudaMalloc((void**)&t->Wlo, b_wlo);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t->grad_slices, b_gs);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t->loss_slices, b_ls);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t->scratch, b_sc);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&t->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(t->err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&t->h_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->err_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    tc_plan_destroy(t);
+    return tcuda(e, "tensor-core workspace");
+  }
+  *t->h_err = 0;
+  t->ws_bytes = b_wh + b_wl + b_wlo + b_gs + b_ls + b_sc;
+  const int R = 128 * t->H;
+  bool ok = encode(&t->wmap, t->Wh, w, w, std::max(1, L - 2), R, 3) &&
+            encode(&t->wlmap, t->Wl, w, p->n_out, 1, 128, 2);
+  if (ok && t->split3) ok = encode(&t->wlomap, t->Wlo, w, w, std::max(1, L - 2), R, 3);
+  if (!ok) {
+    tc_plan_destroy(t);
+    return tfail(JET_ERR_UNSUPPORTED, "tensor map encoding failed");
+  }
+  if (!t->split3) t->wlomap = t->wmap;
+  *out = t;
+  return JET_OK;
+}
+
+void tc_plan_destroy(TcPlan* t) {
+  if (!t) return;
+  cudaFree(t->Wh);
+  cudaFree(t->Wl);
+  cudaFree(t->Wlo);
+  cudaFree(t->grad_slices);
+  cudaFree(t->loss_slices);
+  cudaFree(t->scratch);
+  cudaFree(t->err);
+  cudaFreeHost(t->h_err);
+  if (t->err_ev) cudaEventDestroy(t->err_ev);
+  delete t;
+}
+
+int tc_tile_points(const TcPlan* t) { return t ? t->P : 0; }
+int tc_grid(const TcPlan* t) { return t ? t->grid : 0; }
+size_t tc_workspace_bytes(const TcPlan* t) { return t ? t->ws_bytes : 0; }
+
+namespace {
+
+jet_status check_err(TcPlan* t) {
+  // device-side wait time-outs of an earlier call surface here
+  if (cudaEventQuery(t->err_ev) == cudaSuccess && *t->h_err != 0) {
+    char buf[128];
+    snprintf(buf, sizeof(buf), "a bounded device wait timed out in an earlier call (code %d)", *t->h_err);
+    *t->h_err = 0;
+    cudaMemset(t->err, 0, sizeof(int));
+    jet::set_last_error(buf);
+    return JET_ERR_TIMEOUT;
+  }
+  return JET_OK;
+}
+
+void fill_tc(const jet_plan_s* p, const TcPlan* t, const void* params, const void* X, long long N, const void* source,
+             void* r_out, TcInst& I) {
+  memset(&I, 0, sizeof(I));
+  I.wmap = t->wmap;
+  I.wlmap = t->wlmap;
+  I.wlomap = t->wlomap;
+  I.L = p->L;
+  I.d = p->d;
+  I.n_out = p->n_out;
+  I.n_res = p->n_res;
+  I.w = t->w;
+  I.H = t->H;
+  I.P = t->P;
+  I.cols = t->cols;
+  I.cols_pad = t->cols_pad;
+  I.top_cols = t->top_cols;
+  I.split3 = t->split3;
+  I.n_terms = (int)p->terms.size();
+  for (int m = 0; m < I.n_terms; ++m) I.terms[m] = p->terms[m];
+  I.params = reinterpret_cast<const float*>(params);
+  for (int l = 0; l < p->L; ++l) {
+    I.off_W[l] = p->off_W[l];
+    I.off_b[l] = p->off_b[l];
+  }
+  I.n_params = p->n_params;
+  I.X = reinterpret_cast<const float*>(X);
+  I.source = reinterpret_cast<const float*>(source);
+  I.r_out = reinterpret_cast<float*>(r_out);
+  I.N = N;
+  I.inv_N = N > 0 ? 1.0 / (double)N : 0.0;
+  I.n_tiles = (N + t->P - 1) / t->P;
+  long long chunks = std::min<long long>(std::max<long long>(I.n_tiles, 1), t->grid);
+  I.tiles_per_chunk = (int)((I.n_tiles + chunks - 1) / chunks);
+  if (I.tiles_per_chunk < 1) I.tiles_per_chunk = 1;
+  I.n_chunks = (int)((I.n_tiles + I.tiles_per_chunk - 1) / I.tiles_per_chunk);
+  I.chunk_base = 0;
+  I.grad_slices = t->grad_slices;
+  I.loss_slices = t->loss_slices;
+  I.scratch = t->scratch;
+  I.scratch_stride = t->scratch_stride;
+  I.o_w = t->o_w;
+  I.o_wlo = t->o_wlo;
+  I.o_a0 = t->o_a0;
+  I.o_a1 = t->o_a1;
+  I.o_alo0 = t->o_alo0;
+  I.o_alo1 = t->o_alo1;
+  I.o_uo = t->o_uo;
+  I.o_ub = t->o_ub;
+  I.o_xs = t->o_xs;
+  I.o_red = t->o_red;
+  I.act_bytes = t->act_bytes;
+  I.alo_bytes = t->alo_bytes;
+  I.r0w = t->r0w;
+  I.r1w = t->r1w;
+}
+
+jet_status prep(const jet_plan_s* p, TcPlan* t, const void* params, cudaStream_t s) {
+  OffW ow;
+  for (int l = 0; l < p->L; ++l) ow.v[l] = p->off_W[l];
+  const long long nh = (long long)std::max(0, p->L - 2) * t->w * t->w, nl = (long long)p->n_out * t->w;
+  int grid = (int)std::min<long long>((nh + nl + 255) / 256, 1024);
+  tc_prep_kernel_v<<<grid, 256, 0, s>>>(reinterpret_cast<const float*>(params), p->L, t->w, p->n_out, ow, t->Wh,
+                                        t->Wl, t->Wlo, nh, nl);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? JET_OK : tcuda(e, "tc prep launch");
+}
+
+jet_status run(jet_plan_s* p, TcPlan* t, int mode, const TcInst& I, cudaStream_t s) {
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  a.inst0 = I;
+  a.mode = mode;
+  a.n_items = I.n_chunks;
+  a.insts = nullptr;
+  a.item_inst = nullptr;
+  a.err = t->err;
+  a.tmem_cols = t->tmem_cols;
+  const int grid = std::min(t->grid, I.n_chunks);
+  jet::plan_prof_begin(p, s);
+  cudaError_t e = tc_launch(p->cls, a, grid, t->smem, s);
+  jet::plan_prof_end(p, s);
+  if (e != cudaSuccess) return tcuda(e, "tc kernel launch");
+  e = cudaMemcpyAsync(t->h_err, t->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaEventRecord(t->err_ev, s);
+  return e == cudaSuccess ? JET_OK : tcuda(e, "tc error read-back");
+}
+
+}  // namespace
+
+jet_status tc_forward(jet_plan_s* p, TcPlan* t, const void* params, const void* X, long long N, const void* source,
+                      void* r_out, double* loss_out, cudaStream_t s) {
+  jet_status st = check_err(t);
+  if (st != JET_OK) return st;
+  if (N == 0) {
+    if (loss_out && cudaMemsetAsync(loss_out, 0, sizeof(double), s) != cudaSuccess) return tcuda(cudaGetLastError(), "memset");
+    return JET_OK;
+  }
+  st = prep(p, t, params, s);
+  if (st != JET_OK) return st;
+  TcInst I;
+  fill_tc(p, t, params, X, N, source, r_out, I);
+  st = run(p, t, MODE_FWD, I, s);
+  if (st != JET_OK) return st;
+  if (loss_out) {
+    ReduceJob j;
+    memset(&j, 0, sizeof(j));
+    j.loss_slices = I.loss_slices;
+    j.n_chunks = I.n_chunks;
+    j.inv_N = I.inv_N;
+    j.loss_out = loss_out;
+    cudaError_t e = launch_reduce(nullptr, j, 1, 1, false, false, 1, 0.f, s);
+    if (e != cudaSuccess) return tcuda(e, "reduce");
+  }
+  return JET_OK;
+}
+
+jet_status tc_backward(jet_plan_s* p, TcPlan* t, const void* params, const void* X, long long N, const void* source,
+                       void* grad_out, void* r_out, double* loss_out, cudaStream_t s) {
+  jet_status st = check_err(t);
+  if (st != JET_OK) return st;
+  if (N == 0) {
+    cudaMemsetAsync(grad_out, 0, p->n_params * 4, s);
+    if (loss_out) cudaMemsetAsync(loss_out, 0, sizeof(double), s);
+    return JET_OK;
+  }
+  st = prep(p, t, params, s);
+  if (st != JET_OK) return st;
+  TcInst I;
+  fill_tc(p, t, params, X, N, source, r_out, I);
+  st = run(p, t, MODE_FWD_BWD, I, s);
+  if (st != JET_OK) return st;
+  ReduceJob j;
+  memset(&j, 0, sizeof(j));
+  j.grad_slices = I.grad_slices;
+  j.loss_slices = I.loss_slices;
+  j.n_chunks = I.n_chunks;
+  j.n_params = p->n_params;
+  j.inv_N = I.inv_N;
+  j.grad_out = grad_out;
+  j.loss_out = loss_out;
+  cudaError_t e = launch_reduce(nullptr, j, 1, p->n_params, false, false, 1, 0.f, s);
+  return e == cudaSuccess ? JET_OK : tcuda(e, "reduce");
+}
+
+jet_status tc_train_step(jet_plan_s* p, TcPlan* t, void* params, void* m, void* v, long long step, float lr,
+                         const void* X, long long N, const void* source, double* loss_out, cudaStream_t s) {
+  jet_status st = check_err(t);
+  if (st != JET_OK) return st;
+  st = prep(p, t, params, s);
+  if (st != JET_OK) return st;
+  TcInst I;
+  fill_tc(p, t, params, X, N, source, nullptr, I);
+  st = run(p, t, MODE_FWD_BWD, I, s);
+  if (st != JET_OK) return st;
+  ReduceJob j;
+  memset(&j, 0, sizeof(j));
+  j.grad_slices = I.grad_slices;
+  j.loss_slices = I.loss_slices;
+  j.n_chunks = I.n_chunks;
+  j.n_params = p->n_params;
+  j.inv_N = I.inv_N;
+  j.loss_out = loss_out;
+  j.params = params;
+  j.m = m;
+  j.v = v;
+  cudaError_t e = launch_reduce(nullptr, j, 1, p->n_params, false, true, step, lr, s);
+  return e == cudaSuccess ? JET_OK : tcuda(e, "reduce/adam");
+}
+
+jet_status tc_batch_create(const std::vector<jet_plan_s*>&, TcBatch** out) {
+  *out = nullptr;
+  return tfail(JET_ERR_UNSUPPORTED, "batched tensor-core launches are not provided by this build yet");
+}
+
+void tc_batch_destroy(TcBatch* b) { delete b; }
+
+jet_status tc_batch_run(TcBatch*, const std::vector<jet_plan_s*>&, const void* const*, void* const*, void* const*,
+                        long long, float, const void* const*, const int64_t*, const void* const*, void* const*,
+                        double*, bool, cudaStream_t) {
+  return tfail(JET_ERR_UNSUPPORTED, "batched tensor-core launches are not provided by this build yet");
+}

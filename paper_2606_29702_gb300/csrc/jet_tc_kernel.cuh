@@ -1,0 +1,744 @@
+// Fused tensor-core partial-jet kernel (BF16 operands, FP32 accumulation in
+// TMEM), one persistent launch over (instance, chunk of point tiles) items.
+//
+// Per tile of P collocation points the CTA keeps the jets of one layer in
+// shared memory as a [unit][column] bf16 matrix in the 128-byte-swizzled
+// layout of tc_ptx.cuh, columns = (channel block, point): the channels of the
+// highest derivative order come first, so that the split-precision products
+// of JET_BF16X3 cover one leading column range.  For every hidden layer:
+//
+//   forward  TMA loads W^l (bf16) into shared memory; one thread issues
+//            tcgen05.mma  Z^l[unit][col] = W^l A^{l-1}  (M = 128 units per
+//            half, N = all columns, K = 16 per instruction) into TMEM; the
+//            four epilogue warps read their TMEM lanes (one unit per thread,
+//            all channels of a point in that thread's registers), add the bias
+//            on the value channel, compose the tanh jet in closed form
+//            (Eq. 2-3 recursion) and write A^l back as the next B operand;
+//   output   one more MMA with the output weights (rows >= n_out zero),
+//            residual monomials and the FP64 loss partial;
+//   backward residual adjoint, output-layer gradients, then per layer:
+//            z^l (kept in TMEM for the last layer, recomputed by MMA from the
+//            stored A^{l-1} for the others), activation-jet adjoint in the
+//            epilogue (Zbar^l to shared memory), data gradient
+//            Abar^{l-1} = W^l^T Zbar^l (MN-major A) and weight gradient
+//            Wbar^l = Zbar^l A^{l-1}^T (both operands K-major) by MMA; the
+//            weight gradient is flushed from TMEM into the chunk's FP64 slice.
+//
+// The layer inputs A^l of a tile are saved to a per-CTA global scratch slot by
+// bulk copies during the forward and read back during the backward, so memory
+// is bounded by the number of CTAs.  Every mbarrier wait is bounded: on time-
+// out the kernel records an error code, stops issuing work, waits (bounded) for
+// its own MMAs, releases TMEM and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "jet_closures_gen.h"
+#include "jet_internal.h"
+#include "jet_simt.cuh"
+#include "tc_ptx.cuh"
+
+namespace jet {
+
+constexpr int kTcThreads = 128;
+
+struct alignas(64) TcInst {
+  CUtensorMap wmap;    // hidden weights bf16 [L-2][w][w]: dims (in, out, layer), box (64, R_W, 1)
+  CUtensorMap wlmap;   // output weights bf16 [n_out][w]: dims (in, out), box (64, 128)
+  CUtensorMap wlomap;  // low parts of the hidden weights (JET_BF16X3), like wmap
+  int L, d, n_out, n_res, w, H, P, cols, cols_pad, top_cols, split3;
+  int n_terms;
+  DevTerm terms[kMaxTerms];
+  const float* params;
+  long long off_W[kMaxLayers], off_b[kMaxLayers];
+  long long n_params;
+  const float* X;
+  const float* source;
+  float* r_out;
+  long long N;
+  double inv_N;
+  long long n_tiles;
+  int tiles_per_chunk, n_chunks, chunk_base;
+  double* grad_slices;
+  double* loss_slices;
+  unsigned char* scratch;
+  long long scratch_stride;  // bytes per CTA slot
+  // shared-memory carve (bytes from the 1024-aligned base)
+  int o_w, o_wlo, o_a0, o_a1, o_alo0, o_alo1, o_uo, o_ub, o_xs, o_red;
+  int act_bytes, alo_bytes;
+  int r0w, r1w;  // TMEM column widths of regions R0 and R1 per half
+};
+
+struct TcArgs {
+  TcInst inst0;
+  int mode;
+  int n_items;
+  const TcInst* insts;
+  const int* item_inst;
+  int* err;
+  int tmem_cols;
+};
+
+template <class Cls>
+struct TcTile {
+  static constexpr int C = Cls::C;
+  static constexpr int NP = Cls::NP;
+  static constexpr int TOP = Cls::TOP_BEGIN;
+  static constexpr int PPF = 4;                // points per epilogue pass (forward)
+  static constexpr int PPB = C >= 10 ? 2 : 4;  // points per epilogue pass (adjoint)
+
+  const TcInst& I;
+  unsigned char* sm;
+  uint64_t* bar_tma;
+  uint64_t* bar_mma;
+  uint64_t* bar_ld;
+  volatile int* abort_f;
+  int* err;
+  uint32_t tmem;
+  uint32_t ph_tma, ph_mma, ph_ld;
+  int tid, warp;
+  int R;  // rows of every operand buffer (128 * H)
+
+  // column block of channel c: highest-order channels first
+  static __device__ __forceinline__ int blk(int c) { return c >= TOP ? c - TOP : c + (C - TOP); }
+
+  __device__ float* UO() const { return reinterpret_cast<float*>(sm + I.o_uo); }
+  __device__ float* UB() const { return reinterpret_cast<float*>(sm + I.o_ub); }
+  __device__ float* XS() const { return reinterpret_cast<float*>(sm + I.o_xs); }
+  __device__ unsigned char* ACT(int i) const { return sm + (i ? I.o_a1 : I.o_a0); }
+  __device__ unsigned char* ALO(int i) const { return sm + (i ? I.o_alo1 : I.o_alo0); }
+  __device__ uint32_t R0(int h) const { return tmem + (uint32_t)(h * I.r0w); }
+  __device__ uint32_t R1(int h) const { return tmem + (uint32_t)(I.H * I.r0w + h * I.r1w); }
+  __device__ uint32_t lane_base() const { return (uint32_t)(warp * 32) << 16; }
+
+  __device__ bool wait(uint64_t* bar, uint32_t& ph, int code) {
+    const bool ok = tc::mbar_wait(bar, ph & 1u, abort_f, err, code);
+    ++ph;
+    return ok;
+  }
+
+  __device__ void sync() {
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+  }
+
+  // ------------------------------------------------------------ loads (thread 0)
+  __device__ void load_hidden_w(int l) {  // W^l, l = 2..L-1 -> W buffer (and W_lo)
+    const int nck = I.w / 64 > 2 ? I.w / 64 : 2;
+    const uint32_t box = 64u * R * 2u;
+    tc::mbar_arrive_expect_tx(bar_tma, box * nck * (I.split3 ? 2u : 1u));
+    for (int kc = 0; kc < nck; ++kc) {
+      tc::tma_load_3d(sm + I.o_w + kc * box, &I.wmap, bar_tma, kc * 64, 0, l - 2);
+      if (I.split3) tc::tma_load_3d(sm + I.o_wlo + kc * box, &I.wlomap, bar_tma, kc * 64, 0, l - 2);
+    }
+  }
+
+  __device__ void load_out_w() {  // W^L -> W buffer, 128-row boxes
+    const int nck = (I.w + 63) / 64;
+    const uint32_t box = 64u * 128u * 2u;
+    tc::mbar_arrive_expect_tx(bar_tma, box * nck);
+    for (int kc = 0; kc < nck; ++kc) tc::tma_load_2d(sm + I.o_w + kc * box, &I.wlmap, bar_tma, kc * 64, 0);
+  }
+
+  __device__ unsigned char* slot(int l) const {  // scratch copy of A^l, l = 1..L-3
+    return I.scratch + (long long)blockIdx.x * I.scratch_stride + (long long)(l - 1) * (I.act_bytes + I.alo_bytes);
+  }
+
+  // ------------------------------------------------------------ MMAs (thread 0)
+  // D[R0] = W^l (K-major) x B (MN-major rows = units), plus the split terms
+  __device__ void mma_layer(int bi) {
+    const uint32_t sW = tc::smem_u32(sm + I.o_w), sWlo = tc::smem_u32(sm + I.o_wlo);
+    const uint32_t sB = tc::smem_u32(ACT(bi)), sBlo = tc::smem_u32(ALO(bi));
+    const uint32_t chunkW = (uint32_t)(R / 8) * 1024u, chunkA = chunkW;
+    const uint32_t id = tc::idesc_bf16(128, I.cols_pad, 0, 1);
+    const uint32_t id_top = tc::idesc_bf16(128, I.top_cols, 0, 1);
+    const int ks = I.w / 16;
+    for (int h = 0; h < I.H; ++h) {
+      for (int s = 0; s < ks; ++s) {
+        const uint32_t aoff = (uint32_t)(s / 4) * chunkW + (uint32_t)h * 16384u + (uint32_t)(s % 4) * 32u;
+        const uint64_t ad = tc::sdesc(sW + aoff, 16, 1024);
+        const uint64_t bd = tc::sdesc(sB + (uint32_t)s * 2048u, chunkA, 1024);
+        tc::mma_f16(R0(h), ad, bd, id, s > 0);
+      }
+      if (I.split3) {
+        for (int s = 0; s < ks; ++s) {
+          const uint32_t aoff = (uint32_t)(s / 4) * chunkW + (uint32_t)h * 16384u + (uint32_t)(s % 4) * 32u;
+          tc::mma_f16(R0(h), tc::sdesc(sWlo + aoff, 16, 1024), tc::sdesc(sB + (uint32_t)s * 2048u, chunkA, 1024),
+                      id_top, 1);
+          tc::mma_f16(R0(h), tc::sdesc(sW + aoff, 16, 1024), tc::sdesc(sBlo + (uint32_t)s * 2048u, chunkA, 1024),
+                      id_top, 1);
+        }
+      }
+    }
+  }
+
+  __device__ void mma_out(int bi) {  // D[R1(0)] = W^L (rows >= n_out zero) x A^{L-1}
+    const uint32_t sW = tc::smem_u32(sm + I.o_w), sB = tc::smem_u32(ACT(bi));
+    const uint32_t chunkA = (uint32_t)(R / 8) * 1024u;
+    const uint32_t id = tc::idesc_bf16(128, I.cols_pad, 0, 1);
+    for (int s = 0; s < I.w / 16; ++s) {
+      const uint64_t ad = tc::sdesc(sW + (uint32_t)(s / 4) * 16384u + (uint32_t)(s % 4) * 32u, 16, 1024);
+      const uint64_t bd = tc::sdesc(sB + (uint32_t)s * 2048u, chunkA, 1024);
+      tc::mma_f16(R1(0), ad, bd, id, s > 0);
+    }
+  }
+
+  // D[R1] = W^l^T (MN-major A) x Zbar (MN-major B)
+  __device__ void mma_dgrad(int zi) {
+    const uint32_t sW = tc::smem_u32(sm + I.o_w), sZ = tc::smem_u32(ACT(zi));
+    const uint32_t chunk = (uint32_t)(R / 8) * 1024u;
+    const uint32_t id = tc::idesc_bf16(128, I.cols_pad, 1, 1);
+    for (int h = 0; h < I.H; ++h)
+      for (int s = 0; s < I.w / 16; ++s) {
+        const uint64_t ad = tc::sdesc(sW + (uint32_t)(2 * h) * chunk + (uint32_t)s * 2048u, chunk, 1024);
+        const uint64_t bd = tc::sdesc(sZ + (uint32_t)s * 2048u, chunk, 1024);
+        tc::mma_f16(R1(h), ad, bd, id, s > 0);
+      }
+  }
+
+  // D[R0] = Zbar (K-major, M = out units) x A^{l-1} (K-major, N block nb of in units)
+  __device__ void mma_wgrad(int zi, int ai, int nb, int NB) {
+    const uint32_t sZ = tc::smem_u32(ACT(zi)), sA = tc::smem_u32(ACT(ai));
+    const uint32_t chunk = (uint32_t)(R / 8) * 1024u;
+    const uint32_t id = tc::idesc_bf16(128, NB, 0, 0);
+    for (int h = 0; h < I.H; ++h)
+      for (int s = 0; s < I.cols_pad / 16; ++s) {
+        const uint32_t koff = (uint32_t)(s / 4) * chunk + (uint32_t)(s % 4) * 32u;
+        const uint64_t ad = tc::sdesc(sZ + koff + (uint32_t)h * 16384u, 16, 1024);
+        const uint64_t bd = tc::sdesc(sA + koff + (uint32_t)(nb * NB / 8) * 1024u, 16, 1024);
+        tc::mma_f16(R0(h), ad, bd, id, s > 0);
+      }
+  }
+
+  // ------------------------------------------------------------ epilogue helpers
+  template <int PP>
+  __device__ void st_bf16(unsigned char* buf, int row, int col, const float* v) const {
+    unsigned char* p = buf + tc::swz_off(row, col & ~7, R) + (col & 7) * 2;
+    if (PP == 4) {
+      __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+      __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+      uint2 u;
+      u.x = *reinterpret_cast<uint32_t*>(&a);
+      u.y = *reinterpret_cast<uint32_t*>(&b);
+      *reinterpret_cast<uint2*>(p) = u;
+    } else {
+      __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+      *reinterpret_cast<__nv_bfloat162*>(p) = a;
+    }
+  }
+
+  template <int PP>
+  __device__ void st_lo(unsigned char* buf, int row, int col, const float* v) const {
+    float lo[PP];
+#pragma unroll
+    for (int j = 0; j < PP; ++j) lo[j] = v[j] - __bfloat162float(__float2bfloat16_rn(v[j]));
+    st_bf16<PP>(buf, row, col, lo);
+  }
+
+  // ------------------------------------------------------------ forward pieces
+  __device__ void layer1_fwd(int out_buf) {
+    const float* Pm = I.params;
+    for (int h = 0; h < I.H; ++h) {
+      const int u = h * 128 + tid;
+      if (u >= I.w) continue;
+      float w1[3] = {0.f, 0.f, 0.f};
+      for (int i = 0; i < I.d; ++i) w1[i] = Pm[I.off_W[0] + u * I.d + i];
+      const float b1 = Pm[I.off_b[0] + u];
+      for (int g = 0; g < I.P; g += PPF) {
+        float av[C][PPF];
+#pragma unroll
+        for (int j = 0; j < PPF; ++j) {
+          float z[C], p[NP], a[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) z[c] = 0.f;
+          float v = b1;
+          for (int i = 0; i < I.d; ++i) v = fmaf(w1[i], XS()[(g + j) * I.d + i], v);
+          z[0] = v;
+#pragma unroll
+          for (int i = 0; i < Cls::D; ++i) {
+            const int fo = Cls::first_order(i);
+            if (fo >= 0) z[fo] = w1[i];
+          }
+          tanh_derivs<float, NP>(z[0], p);
+          Cls::compose(z, p, a);
+#pragma unroll
+          for (int c = 0; c < C; ++c) av[c][j] = a[c];
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          st_bf16<PPF>(ACT(out_buf), u, blk(c) * I.P + g, av[c]);
+          if (I.split3 && c >= TOP) st_lo<PPF>(ALO(out_buf), u, blk(c) * I.P + g, av[c]);
+        }
+      }
+    }
+  }
+
+  // a^l = compose(D[R0] + b^l) -> ACT(out_buf)
+  __device__ void hidden_epilogue(int l, int out_buf) {
+    for (int h = 0; h < I.H; ++h) {
+      const int u = h * 128 + tid;
+      if (h * 128 + warp * 32 >= I.w) continue;  // warp-uniform
+      const float bu = I.params[I.off_b[l - 1] + u];
+      for (int g = 0; g < I.P; g += PPF) {
+        float zv[C][PPF];
+#pragma unroll
+        for (int c = 0; c < C; ++c) tc::tmem_ld<PPF>(R0(h) + lane_base() + (uint32_t)(blk(c) * I.P + g), zv[c]);
+        tc::tmem_wait_ld();
+        float av[C][PPF];
+#pragma unroll
+        for (int j = 0; j < PPF; ++j) {
+          float z[C], p[NP], a[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) z[c] = zv[c][j];
+          z[0] += bu;
+          tanh_derivs<float, NP>(z[0], p);
+          Cls::compose(z, p, a);
+#pragma unroll
+          for (int c = 0; c < C; ++c) av[c][j] = a[c];
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          st_bf16<PPF>(ACT(out_buf), u, blk(c) * I.P + g, av[c]);
+          if (I.split3 && c >= TOP) st_lo<PPF>(ALO(out_buf), u, blk(c) * I.P + g, av[c]);
+        }
+      }
+    }
+  }
+
+  __device__ void out_epilogue() {  // warp 0: UO[o*C + c][n] = D[R1(0)] (+ b^L on the value channel)
+    if (warp != 0) return;
+    float* uo = UO();
+    for (int c = 0; c < C; ++c)
+      for (int g = 0; g < I.P; g += 8) {
+        float v[8];
+        tc::tmem_ld8(R1(0) + (uint32_t)(blk(c) * I.P + g), v);
+        tc::tmem_wait_ld();
+        if (tid < I.n_out) {
+          const float b = c == 0 ? I.params[I.off_b[I.L - 1] + tid] : 0.f;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) uo[(tid * C + c) * I.P + g + j] = v[j] + b;
+        }
+      }
+  }
+
+  __device__ double residual(long long n0, int nvalid, bool bwd) {
+    float* uo = UO();
+    float* ub = UB();
+    const int P = I.P;
+    double loss = 0.0;
+    if (bwd)
+      for (int i = tid; i < I.n_out * C * P; i += kTcThreads) ub[i] = 0.f;
+    __syncthreads();
+    for (int n = tid; n < nvalid; n += kTcThreads) {
+      float r[kMaxRes];
+      for (int c = 0; c < I.n_res; ++c) r[c] = I.source ? -I.source[(n0 + n) * I.n_res + c] : 0.f;
+      for (int m = 0; m < I.n_terms; ++m) {
+        const DevTerm& tm = I.terms[m];
+        float prod = (float)tm.coef;
+        for (int f = 0; f < tm.nfac; ++f) prod *= uo[tm.fac[f] * P + n];
+        r[tm.comp] += prod;
+      }
+      for (int c = 0; c < I.n_res; ++c) {
+        if (I.r_out) I.r_out[(n0 + n) * I.n_res + c] = r[c];
+        loss += (double)r[c] * (double)r[c];
+      }
+      if (bwd) {
+        const float two_over_n = (float)(2.0 * I.inv_N);
+        for (int m = 0; m < I.n_terms; ++m) {
+          const DevTerm& tm = I.terms[m];
+          const float gg = two_over_n * r[tm.comp] * (float)tm.coef;
+          for (int f = 0; f < tm.nfac; ++f) {
+            float prod = gg;
+            for (int q = 0; q < tm.nfac; ++q)
+              if (q != f) prod *= uo[tm.fac[q] * P + n];
+            ub[tm.fac[f] * P + n] += prod;
+          }
+        }
+      }
+    }
+    return loss;
+  }
+
+  // ------------------------------------------------------------ backward pieces
+  // dW^L[o][k] += sum_cols ub[o][col] a^{L-1}[k][col]; db^L[o] += sum_n ub[o][0][n]
+  __device__ void out_grads(int a_buf, double* g) {
+    const float* ub = UB();
+    const int P = I.P, L = I.L;
+    for (int h = 0; h < I.H; ++h) {
+      const int k = h * 128 + tid;
+      if (k >= I.w) continue;
+      float acc[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
+      for (int c = 0; c < C; ++c)
+        for (int q = 0; q < P; q += 8) {
+          const int col = blk(c) * P + q;
+          const uint4 raw = *reinterpret_cast<const uint4*>(ACT(a_buf) + tc::swz_off(k, col, R));
+          const __nv_bfloat16* bv = reinterpret_cast<const __nv_bfloat16*>(&raw);
+          for (int o = 0; o < I.n_out; ++o)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[o] = fmaf(__bfloat162float(bv[j]), ub[(o * C + c) * P + q + j], acc[o]);
+        }
+      for (int o = 0; o < I.n_out; ++o) tc::red_add_f64(g + I.off_W[L - 1] + (long long)o * I.w + k, (double)acc[o]);
+    }
+    if (tid < I.n_out) {
+      float s = 0.f;
+      for (int n = 0; n < P; ++n) s += ub[(tid * C + 0) * P + n];
+      tc::red_add_f64(g + I.off_b[L - 1] + tid, (double)s);
+    }
+  }
+
+  // Zbar^l = (d compose/dz)^T Abar^l -> ACT(z_buf); db^l += sum_n Zbar_0
+  __device__ void adjoint_epilogue(int l, int z_buf, bool abar_from_ub, double* g) {
+    const float* ub = UB();
+    const int P = I.P;
+    for (int h = 0; h < I.H; ++h) {
+      const int u = h * 128 + tid;
+      if (h * 128 + warp * 32 >= I.w) continue;
+      const float bu = I.params[I.off_b[l - 1] + u];
+      float wl[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
+      if (abar_from_ub)
+        for (int o = 0; o < I.n_out; ++o) wl[o] = I.params[I.off_W[I.L - 1] + (long long)o * I.w + u];
+      float gb = 0.f;
+      for (int q = 0; q < P; q += PPB) {
+        float zv[C][PPB], abv[C][PPB];
+#pragma unroll
+        for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R0(h) + lane_base() + (uint32_t)(blk(c) * P + q), zv[c]);
+        if (!abar_from_ub) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R1(h) + lane_base() + (uint32_t)(blk(c) * P + q), abv[c]);
+        }
+        tc::tmem_wait_ld();
+        if (abar_from_ub) {
+#pragma unroll
+          for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int j = 0; j < PPB; ++j) {
+              float s = 0.f;
+              for (int o = 0; o < I.n_out; ++o) s = fmaf(wl[o], ub[(o * C + c) * P + q + j], s);
+              abv[c][j] = s;
+            }
+        }
+        float zbv[C][PPB];
+#pragma unroll
+        for (int j = 0; j < PPB; ++j) {
+          float z[C], p[NP], ab[C], zb[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            z[c] = zv[c][j];
+            ab[c] = abv[c][j];
+          }
+          z[0] += bu;
+          tanh_derivs<float, NP>(z[0], p);
+          Cls::adjoint(z, p, ab, zb);
+#pragma unroll
+          for (int c = 0; c < C; ++c) zbv[c][j] = zb[c];
+          gb += zb[0];
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) st_bf16<PPB>(ACT(z_buf), u, blk(c) * P + q, zbv[c]);
+      }
+      if (u < I.w) tc::red_add_f64(g + I.off_b[l - 1] + u, (double)gb);
+    }
+  }
+
+  // D[R0] (weight gradient block nb of layer l) -> FP64 slice
+  __device__ void flush_wgrad(int l, int nb, int NB, double* g) {
+    double* gW = g + I.off_W[l - 1];
+    for (int h = 0; h < I.H; ++h) {
+      if (h * 128 + warp * 32 >= I.w) continue;
+      const int j = h * 128 + tid;
+      for (int k0 = 0; k0 < NB; k0 += 8) {
+        float v[8];
+        tc::tmem_ld8(R0(h) + lane_base() + (uint32_t)k0, v);
+        tc::tmem_wait_ld();
+        const int k = nb * NB + k0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (k + i < I.w) tc::red_add_f64(gW + (long long)j * I.w + k + i, (double)v[i]);
+      }
+    }
+  }
+
+  // layer-1 backward with z^1 recomputed from the points
+  __device__ void layer1_bwd(bool abar_from_ub, double* g) {
+    const float* Pm = I.params;
+    const float* ub = UB();
+    const int P = I.P;
+    for (int h = 0; h < I.H; ++h) {
+      const int u = h * 128 + tid;
+      if (h * 128 + warp * 32 >= I.w) continue;
+      float w1[3] = {0.f, 0.f, 0.f};
+      for (int i = 0; i < I.d; ++i) w1[i] = Pm[I.off_W[0] + u * I.d + i];
+      const float b1 = Pm[I.off_b[0] + u];
+      float wl[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
+      if (abar_from_ub)
+        for (int o = 0; o < I.n_out; ++o) wl[o] = Pm[I.off_W[I.L - 1] + (long long)o * I.w + u];
+      float gw[3] = {0.f, 0.f, 0.f}, gb = 0.f;
+      for (int q = 0; q < P; q += PPB) {
+        float abv[C][PPB];
+        if (!abar_from_ub) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R1(h) + lane_base() + (uint32_t)(blk(c) * P + q), abv[c]);
+          tc::tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int j = 0; j < PPB; ++j) {
+              float s = 0.f;
+              for (int o = 0; o < I.n_out; ++o) s = fmaf(wl[o], ub[(o * C + c) * P + q + j], s);
+              abv[c][j] = s;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PPB; ++j) {
+          float z[C], p[NP], ab[C], zb[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            z[c] = 0.f;
+            ab[c] = abv[c][j];
+          }
+          float v = b1;
+          for (int i = 0; i < I.d; ++i) v = fmaf(w1[i], XS()[(q + j) * I.d + i], v);
+          z[0] = v;
+#pragma unroll
+          for (int i = 0; i < Cls::D; ++i) {
+            const int fo = Cls::first_order(i);
+            if (fo >= 0) z[fo] = w1[i];
+          }
+          tanh_derivs<float, NP>(z[0], p);
+          Cls::adjoint(z, p, ab, zb);
+          gb += zb[0];
+          for (int i = 0; i < I.d; ++i) gw[i] = fmaf(zb[0], XS()[(q + j) * I.d + i], gw[i]);
+#pragma unroll
+          for (int i = 0; i < Cls::D; ++i) {
+            const int fo = Cls::first_order(i);
+            if (fo >= 0) gw[i] += zb[fo];
+          }
+        }
+      }
+      for (int i = 0; i < I.d; ++i) tc::red_add_f64(g + I.off_W[0] + (long long)u * I.d + i, (double)gw[i]);
+      tc::red_add_f64(g + I.off_b[0] + u, (double)gb);
+    }
+  }
+
+  // ------------------------------------------------------------ one tile
+  __device__ double tile(long long t, int mode, double* g) {
+    const int P = I.P, L = I.L, d = I.d;
+    const bool bwd = mode != MODE_FWD;
+    const long long n0 = t * P;
+    const long long rem = I.N - n0;
+    const int nvalid = rem < (long long)P ? (int)rem : P;
+    float* xs = XS();
+    for (int i = tid; i < P * d; i += kTcThreads) {
+      const int n = i / d;
+      xs[i] = n < nvalid ? I.X[(n0 + n) * d + (i % d)] : 0.f;
+    }
+    if (tid == 0 && !*abort_f) {
+      tc::bulk_wait_read0();  // earlier bulk stores must have read ACT(0) before it is rewritten
+      if (L >= 3) load_hidden_w(2);
+      else load_out_w();
+    }
+    __syncthreads();
+    // ---- forward
+    layer1_fwd(0);
+    tc::fence_proxy_async_smem();
+    sync();
+    // scratch keeps A^l for l <= L-3 (A^{L-2} stays in shared memory for the backward)
+    if (tid == 0 && bwd && L >= 4 && !*abort_f) {
+      tc::bulk_s2g(slot(1), ACT(0), (uint32_t)I.act_bytes);
+      if (I.split3) tc::bulk_s2g(slot(1) + I.act_bytes, ALO(0), (uint32_t)I.alo_bytes);
+      tc::bulk_commit();
+    }
+    int cur = 0;
+    for (int l = 2; l <= L - 1; ++l) {
+      if (!wait(bar_tma, ph_tma, 10 + l)) break;
+      if (tid == 0) {
+        tc::bulk_wait_read0();  // ACT(cur^1) is about to be rewritten
+        tc::tc_fence_after();
+        mma_layer(cur);
+        tc::mma_commit(bar_mma);
+      }
+      if (!wait(bar_mma, ph_mma, 30 + l)) break;
+      tc::tc_fence_after();
+      if (tid == 0) {
+        if (l + 1 <= L - 1) load_hidden_w(l + 1);
+        else load_out_w();
+      }
+      hidden_epilogue(l, cur ^ 1);
+      tc::fence_proxy_async_smem();
+      sync();
+      if (tid == 0 && bwd && l <= L - 3) {
+        tc::bulk_s2g(slot(l), ACT(cur ^ 1), (uint32_t)I.act_bytes);
+        if (I.split3) tc::bulk_s2g(slot(l) + I.act_bytes, ALO(cur ^ 1), (uint32_t)I.alo_bytes);
+        tc::bulk_commit();
+      }
+      cur ^= 1;
+    }
+    // ---- output layer
+    if (!*abort_f && wait(bar_tma, ph_tma, 50)) {
+      if (tid == 0) {
+        tc::tc_fence_after();
+        mma_out(cur);
+        tc::mma_commit(bar_mma);
+      }
+      if (wait(bar_mma, ph_mma, 51)) {
+        tc::tc_fence_after();
+        if (tid == 0 && bwd && L >= 3) load_hidden_w(L - 1);
+        out_epilogue();
+      }
+    }
+    sync();
+    double loss = 0.0;
+    if (!*abort_f) loss = residual(n0, nvalid, bwd);
+    __syncthreads();
+    if (!bwd || *abort_f) return loss;
+    // ---- backward
+    out_grads(cur, g);
+    __syncthreads();
+    const int zb = cur, ain = cur ^ 1;
+    for (int l = L - 1; l >= 2; --l) {
+      if (l < L - 1) {
+        // reload A^{l-1} and W^l, recompute z^l = W^l A^{l-1} into R0
+        if (tid == 0) {
+          tc::bulk_wait0();
+          tc::mbar_arrive_expect_tx(bar_ld, (uint32_t)(I.act_bytes + (I.split3 ? I.alo_bytes : 0)));
+          tc::bulk_g2s(ACT(ain), slot(l - 1), (uint32_t)I.act_bytes, bar_ld);
+          if (I.split3) tc::bulk_g2s(ALO(ain), slot(l - 1) + I.act_bytes, (uint32_t)I.alo_bytes, bar_ld);
+          load_hidden_w(l);
+        }
+        if (!wait(bar_ld, ph_ld, 60)) break;
+        if (!wait(bar_tma, ph_tma, 61)) break;
+        if (tid == 0) {
+          tc::tc_fence_after();
+          mma_layer(ain);
+          tc::mma_commit(bar_mma);
+        }
+        if (!wait(bar_mma, ph_mma, 62)) break;
+        tc::tc_fence_after();
+      } else {
+        if (!wait(bar_tma, ph_tma, 63)) break;  // W^{L-1} for the data gradient
+      }
+      adjoint_epilogue(l, zb, l == L - 1, g);
+      tc::fence_proxy_async_smem();
+      sync();
+      const int NB = I.H == 2 ? 128 : I.w;
+      const int nblk = I.w / NB;
+      if (tid == 0) {
+        mma_dgrad(zb);
+        mma_wgrad(zb, ain, 0, NB);
+        tc::mma_commit(bar_mma);
+      }
+      if (!wait(bar_mma, ph_mma, 64)) break;
+      tc::tc_fence_after();
+      flush_wgrad(l, 0, NB, g);
+      for (int nb = 1; nb < nblk; ++nb) {
+        sync();
+        if (tid == 0) {
+          mma_wgrad(zb, ain, nb, NB);
+          tc::mma_commit(bar_mma);
+        }
+        if (!wait(bar_mma, ph_mma, 65)) break;
+        tc::tc_fence_after();
+        flush_wgrad(l, nb, NB, g);
+      }
+      sync();
+    }
+    if (!*abort_f) layer1_bwd(L == 2, g);
+    sync();
+    return loss;
+  }
+};
+
+template <class Cls>
+__global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant__ TcArgs args) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t bars[3];
+  __shared__ uint32_t tmem_s;
+  __shared__ volatile int abort_s;
+  __shared__ double red_s[kTcThreads / 32];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    abort_s = 0;
+    tc::mbar_init(&bars[0], 1);
+    tc::mbar_init(&bars[1], 1);
+    tc::mbar_init(&bars[2], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_s, (uint32_t)args.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  uint32_t ph_tma = 0, ph_mma = 0, ph_ld = 0;
+  int prev_inst = -1;
+  for (int k = blockIdx.x; k < args.n_items && !abort_s; k += gridDim.x) {
+    const int item = args.item_inst ? args.item_inst[k] : k;
+    const int ii = args.insts ? args.item_inst[args.n_items + item] : 0;
+    const TcInst& I = args.insts ? args.insts[ii] : args.inst0;
+    const int chunk = item - I.chunk_base;
+    if (ii != prev_inst) {
+      // zero both activation buffers (and split buffers) once per instance:
+      // padding rows and columns must read as zero in every MMA
+      const int R = 128 * I.H;
+      (void)R;
+      uint4 z4 = make_uint4(0, 0, 0, 0);
+      for (int i = tid; i < I.act_bytes / 16; i += kTcThreads) {
+        reinterpret_cast<uint4*>(sm + I.o_a0)[i] = z4;
+        reinterpret_cast<uint4*>(sm + I.o_a1)[i] = z4;
+      }
+      if (I.split3)
+        for (int i = tid; i < I.alo_bytes / 16; i += kTcThreads) {
+          reinterpret_cast<uint4*>(sm + I.o_alo0)[i] = z4;
+          reinterpret_cast<uint4*>(sm + I.o_alo1)[i] = z4;
+        }
+      if (tid == 0) {
+        tc::prefetch_tensormap(&I.wmap);
+        tc::prefetch_tensormap(&I.wlmap);
+      }
+      tc::fence_proxy_async_smem();
+      __syncthreads();
+      prev_inst = ii;
+    }
+    TcTile<Cls> T{I, sm, &bars[0], &bars[1], &bars[2], &abort_s, args.err, tmem_s, ph_tma, ph_mma, ph_ld, tid, warp,
+                  128 * I.H};
+    const bool bwd = args.mode != MODE_FWD;
+    double* g = bwd ? I.grad_slices + (long long)chunk * I.n_params : nullptr;
+    if (bwd)
+      for (long long i = tid; i < I.n_params; i += kTcThreads) g[i] = 0.0;
+    __syncthreads();
+    double loss = 0.0;
+    const long long t0 = (long long)chunk * I.tiles_per_chunk;
+    const long long t1 = (t0 + I.tiles_per_chunk < I.n_tiles) ? t0 + I.tiles_per_chunk : I.n_tiles;
+    for (long long t = t0; t < t1 && !abort_s; ++t) loss += T.tile(t, args.mode, g);
+    ph_tma = T.ph_tma;
+    ph_mma = T.ph_mma;
+    ph_ld = T.ph_ld;
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
+    if ((tid & 31) == 0) red_s[warp] = loss;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < kTcThreads / 32; ++w) s += red_s[w];
+      I.loss_slices[chunk] = s;
+    }
+    __syncthreads();
+  }
+  // teardown: drain our own bulk copies and MMAs (bounded), release TMEM
+  if (tid == 0) tc::bulk_wait0();
+  if (abort_s && tid == 0) {
+    volatile int dummy = 0;
+    tc::mma_commit(&bars[1]);
+    tc::mbar_wait(&bars[1], ph_mma & 1u, &dummy, args.err, 99, 100000000ull);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem_s, (uint32_t)args.tmem_cols);
+}
+
+}  // namespace jet
