@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--workload", default="ks_2x64x5")
     ap.add_argument("--form", default=None, help="precision form of the headline (default: the workload's)")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="0 skips the oracle leg")
+    ap.add_argument("--n", type=int, default=None, help="override the workload's point count (profiling)")
     return ap.parse_args()
 
 
@@ -72,9 +73,17 @@ def max_over_ranks(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(ms_local, n_local, ws):
+    """(max step time over ranks, whole-job points/s): every rank runs an
+    independent replica of n_local points, timed by the slowest rank."""
+    ms = max_over_ranks(ms_local, ws)
+    return ms, ws * n_local / (ms * 1e-3)
 
 
 def flops_per_point(widths, C):
@@ -152,6 +161,22 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def roofline(form, flops, kernel_ms, peaks, peak_kind):
+    """Roofline of the dominant kernel: algorithmic jet-GEMM flops / its event time."""
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    if form in ("fp32", "fp64"):
+        peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) if form == "fp32" else \
+            fp64_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "fused SIMT jet kernel (%s)" % form,
+                "peak_kind": "derived: 152 SM x %s lanes x 2 flop x max clock" % ("128 FP32" if form == "fp32"
+                                                                                 else "2 FP64")}
+    peak = peaks["bf16_tflops"] * (0.5 if form == "tf32" else 1.0)
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "tcgen05 fused jet kernel (%s)" % form,
+            "peak_kind": "%s bf16_tflops (burst)" % peak_kind}
+
+
 def fp64_alu_peak_tflops(sm_mhz=2070.0, sms=152):
     """FP64 FMA peak: 152 SMs x 2 FP64 lanes per SM partition quad (64 FP64
     flops/clk/SM on GB300 per unit count ratio 1:64 of FP32) -- reported for
@@ -208,8 +233,9 @@ def _blas_threads():
     return os.cpu_count() or 1
 
 
-def cpu_baseline(spec, seconds):
-    """Oracle points/s on the host cores over a bounded sample (~`seconds` s)."""
+def cpu_baseline(spec, seconds, forms=()):
+    """Oracle points/s on the host cores over a bounded sample (~`seconds` s),
+    and the relative error against it of every GPU form on the same sample."""
     import oracle
     from oracle import residuals as R
     from paper_2606_29702_gb300 import workloads as wl
@@ -218,14 +244,40 @@ def cpu_baseline(spec, seconds):
     layers = wl.xavier_layers(spec["widths"], spec["seed_par"])
     fam = R.by_name(spec["family"], **spec["coefs"])
     src = R.helmholtz_source(X, spec["coefs"]["k"])[:, None] if spec["family"] == "helmholtz" else None
-    oracle.loss_and_grad(fam, layers, X, source=src)
+    L_ref, r_ref, g_ref = oracle.loss_and_grad(fam, layers, X, source=src)
+    g_ref = wl.pack(g_ref)
     n, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds:
         oracle.loss_and_grad(fam, layers, X, source=src)
         n += 1
     dt = time.perf_counter() - t0
-    return {"value": n * S / dt, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
-            "sample": "%d runs of residual+gradient on %d points of the workload (%.1f s)" % (n, S, dt)}
+    errs = {}
+    for f in forms:
+        try:
+            r, g = gpu_sample(spec, f, X, layers, src)
+            errs[f] = {"residual_rel_l2": float(np.linalg.norm(r - r_ref) / np.linalg.norm(r_ref)),
+                       "gradient_rel_l2": float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))}
+        except Exception as e:  # a form this build does not provide
+            errs[f] = {"unavailable": str(e).splitlines()[0][:120]}
+    return {"value": n * S / max(dt, 1e-9), "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
+            "sample": "%d runs of residual+gradient on %d points of the workload (%.1f s)" % (n, S, dt)}, errs
+
+
+def gpu_sample(spec, form, X, layers, src):
+    """Residual and gradient of one GPU form on the sample points (float64 numpy)."""
+    import torch
+    from paper_2606_29702_gb300 import jet, specs
+    from paper_2606_29702_gb300 import workloads as wl
+    plan = jet.Plan(specs.by_name(spec["family"], **spec["coefs"]), spec["widths"], form)
+    dt = plan.dtype
+    p = torch.tensor(wl.pack(layers), dtype=dt, device="cuda")
+    x = torch.tensor(X, dtype=dt, device="cuda")
+    s = None if src is None else torch.tensor(src, dtype=dt, device="cuda")
+    g, _, r = plan.backward(p, x, s, want_r=True)
+    torch.cuda.synchronize()
+    out = r.cpu().double().numpy(), g.cpu().double().numpy()
+    plan.close()
+    return out
 
 
 # ------------------------------------------------------------------ ours
@@ -304,6 +356,8 @@ def run_ours(args, rank, ws, local):
     import torch
     from paper_2606_29702_gb300 import workloads as wl
     spec = dict(wl.WORKLOADS[args.workload])
+    if args.n:
+        spec["N"] = args.n
     form = args.form or spec["precision"]
     X = wl.points(spec["domain"], spec["N"], spec["seed_pts"] + rank)
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -320,31 +374,21 @@ def run_ours(args, rank, ws, local):
     torch.cuda.synchronize()
     barrier(ws)
     clk = clocks.stop()
-    ms = max_over_ranks(res["ms_per_step"], ws)
-    value = ws * spec["N"] / (ms * 1e-3)
+    ms, value = aggregate(res["ms_per_step"], spec["N"], ws)
     C = res["info"]["n_channels"]
     fpp = flops_per_point(spec["widths"], C)
     peaks, peak_kind = measured_peaks()
-    kernel_ms = res["kernel_ms"]
-    achieved = fpp * spec["N"] / (kernel_ms * 1e-3) / 1e12
-    if form in ("fp32", "fp64"):
-        peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) if form == "fp32" else \
-            fp64_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
-                "kernel": "fused SIMT jet kernel (%s)" % form, "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x max clock"}
-    else:
-        peak = peaks["bf16_tflops"] * (0.5 if form == "tf32" else 1.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "tcgen05 jet kernel (%s)" % form, "peak_kind": peak_kind}
+    roof = roofline(form, fpp * spec["N"], res["kernel_ms"], peaks, peak_kind)
     forms = {}
     if not args.no_forms and rank == 0:
-        for f in ("fp32", "bf16", "tf32", "fp64"):
+        for f in ("fp32", "bf16", "bf16x3", "tf32", "fp64"):
             if f == form:
                 continue
             try:
                 r = time_form(spec, f, X, max(3, args.steps // 2), 3, flush, want_kernel=True)
-                forms[f] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernel_ms": r["kernel_ms"]}
+                forms[f] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernel_ms": r["kernel_ms"],
+                            "tile_points": r["info"]["tile_points"], "grid_ctas": r["info"]["grid_ctas"],
+                            "roofline": roofline(f, fpp * spec["N"], r["kernel_ms"], peaks, peak_kind)}
             except Exception as e:  # a form this build does not provide
                 forms[f] = {"unavailable": str(e).splitlines()[0][:160]}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -358,7 +402,11 @@ def run_ours(args, rank, ws, local):
            "e2e": res["e2e"], "gpu_launches": 3 * args.steps, "roofline": roof, "clocks": clk,
            "forms": forms}
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(spec, args.cpu_seconds) if ws == 1 else None
+        if ws == 1 and args.cpu_seconds > 0:
+            out["cpu_baseline"], out["rel_err_vs_fp64"] = cpu_baseline(
+                spec, args.cpu_seconds, [form] + [f for f in forms if "unavailable" not in forms[f]])
+        else:
+            out["cpu_baseline"] = None
         print(json.dumps(out))
 
 

@@ -76,6 +76,11 @@ typedef enum {
 #define JET_FLAG_STORE 0x2       /* jet_forward_residual keeps the hidden z-jets
                                     (if they fit the budget) for the next
                                     jet_backward_params on the same inputs */
+/* Tile override (used by the autotuner): points per tile of the fused kernel,
+ * P = 8 * JET_FLAG_TILE_GET(flags) when nonzero.  The plan rejects a P its
+ * kernel cannot run (JET_ERR_UNSUPPORTED); 0 keeps the built-in choice. */
+#define JET_FLAG_TILE(p8) (((p8)&0xff) << 8)
+#define JET_FLAG_TILE_GET(flags) (((flags) >> 8) & 0xff)
 
 /* One derivative channel d^alpha u_out: alpha[i] = order in coordinate i. */
 typedef struct {

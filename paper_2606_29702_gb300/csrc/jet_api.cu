@@ -166,10 +166,7 @@ int pitch_for(int cols, bool fp64) {
 }
 
 size_t smem_bytes(int C, int P, int pitch, int wmax, int n_out, int d, size_t elem) {
-  size_t e = 3 * (size_t)wmax * pitch + 2 * (size_t)n_out * C * P + (size_t)P * d;
-  size_t bytes = e * elem;
-  bytes = (bytes + 15) / 16 * 16;
-  return bytes + 64 * sizeof(double);
+  return simt_smem_bytes(C, P, pitch, wmax, n_out, d, elem);
 }
 
 }  // namespace
@@ -296,7 +293,8 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
   // ---- tiling and occupancy of the fused SIMT kernel
   int wmax = 0;
   for (int l = 1; l < n_layers; ++l) wmax = std::max(wmax, widths[l]);
-  p->P = tile_points(p->C, wmax, p->fp64);
+  const int p8 = JET_FLAG_TILE_GET(flags);
+  p->P = p8 ? 8 * p8 : tile_points(p->C, wmax, p->fp64);
   p->pitch = pitch_for(p->C * p->P, p->fp64);
   p->smem = smem_bytes(p->C, p->P, p->pitch, wmax, n_out, d_in, p->elem);
   cudaDeviceProp prop;
@@ -604,6 +602,10 @@ struct jet_batch_s {
   ReduceJob* h_jobs = nullptr;
   int max_items = 0;
   TcBatch* tcb = nullptr;
+  // the pinned staging buffers are rewritten by the next call only after the
+  // uploads of this one have read them
+  cudaEvent_t copied = nullptr;
+  bool have_prev = false;
 };
 
 namespace {
@@ -620,6 +622,7 @@ void free_batch(jet_batch_s* b) {
   cudaFreeHost(b->h_item_inst);
   cudaFreeHost(b->h_jobs);
   if (b->tcb) tc_batch_destroy(b->tcb);
+  if (b->copied) cudaEventDestroy(b->copied);
 }
 
 // Build the per-call work list: every instance is split into chunks of point
@@ -634,6 +637,9 @@ jet_status batch_prepare(jet_batch_s* b, const void* const* params, const void* 
     if (st != JET_OK) return st;
     total_tiles += (N[i] + b->plans[i]->P - 1) / b->plans[i]->P;
   }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (b->have_prev && cs == cudaStreamCaptureStatusNone) cudaEventSynchronize(b->copied);
   // target about four items per CTA
   long long target_tiles = std::max<long long>(1, (total_tiles + 4LL * b->grid - 1) / (4LL * b->grid));
   std::vector<std::pair<double, int>> cost;  // (cost, item) for ordering
@@ -779,6 +785,13 @@ static jet_status batch_run(jet_batch_t b, const void* const* params, void* cons
     maxp = std::max(maxp, j.n_params);
   }
   CK(cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(ReduceJob) * n, cudaMemcpyHostToDevice, s));
+  if (!b->copied) CK(cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming));
+  cudaStreamCaptureStatus cs2 = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs2);
+  if (cs2 == cudaStreamCaptureStatusNone) {  // a captured upload replays from the staging of the latest call
+    CK(cudaEventRecord(b->copied, s));
+    b->have_prev = true;
+  }
   CK(launch_reduce(b->d_jobs, b->h_jobs[0], n, maxp, b->fp64, adam, step, lr, s));
   return JET_OK;
 }

@@ -74,6 +74,14 @@ struct SimtArgs {
 };
 
 constexpr int kSimtThreads = 256;
+// Dynamic shared memory of the fused SIMT kernel: three jet buffers
+// [wmax][pitch], output jets and adjoints [n_out*C][P], tile points [P][d],
+// and a small reduction area.
+inline size_t simt_smem_bytes(int C, int P, int pitch, int wmax, int n_out, int d, size_t elem) {
+  size_t e = 3 * (size_t)wmax * pitch + 2 * (size_t)n_out * C * P + (size_t)P * d;
+  size_t bytes = (e * elem + 15) / 16 * 16;
+  return bytes + 64 * sizeof(double);
+}
 
 
 // Reductions and elementwise kernels (jet_reduce.cu)

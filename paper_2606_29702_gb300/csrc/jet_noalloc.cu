@@ -203,8 +203,7 @@ extern "C" jet_status jet_backward_params_noalloc(const jet_residual_spec* spec,
   I.P = P;
   I.pitch = pitch;
   I.n_tiles = (N + P - 1) / P;
-  size_t smem = (3 * (size_t)wmax * pitch + 2 * (size_t)n_out * C * P + (size_t)P * d_in) * elem;
-  smem = (smem + 15) / 16 * 16 + 64 * sizeof(double);
+  const size_t smem = simt_smem_bytes(C, P, pitch, wmax, n_out, d_in, elem);
   long long jet_elems = 0;
   for (int l = 1; l < n_layers; ++l) jet_elems += (long long)C * P * widths[l];
 

@@ -216,12 +216,18 @@ struct SimtTile {
     const int ngrp = P / TP;
     for (int it = threadIdx.x; it < w * ngrp; it += NT) {
       const int u = it % w, pg = it / w;
+      // all loads of the point group first, so that they are in flight together
+      T zz[C][TP];
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int j = 0; j < TP; ++j) zz[c][j] = zsrc[(long long)(c * P + pg * TP + j) * w + u];
       T outv[C][TP];
 #pragma unroll
       for (int j = 0; j < TP; ++j) {
         T z[C], p[NP], a[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) z[c] = zsrc[(long long)(c * P + pg * TP + j) * w + u];
+        for (int c = 0; c < C; ++c) z[c] = zz[c][j];
         tanh_derivs<T, NP>(z[0], p);
         Cls::compose(z, p, a);
 #pragma unroll
@@ -316,7 +322,12 @@ struct SimtTile {
     const int ngrp = P / TP;
     for (int it = threadIdx.x; it < w * ngrp; it += NT) {
       const int u = it % w, pg = it / w;
-      T abv[C][TP], outv[C][TP];
+      T abv[C][TP], outv[C][TP], zz[C][TP];
+      // all global loads of the point group first, so that they overlap
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int j = 0; j < TP; ++j) zz[c][j] = zsrc[(long long)(c * P + pg * TP + j) * w + u];
 #pragma unroll
       for (int c = 0; c < C; ++c) vload<T>(abar + u * pitch + c * P + pg * TP, abv[c]);
 #pragma unroll
@@ -324,7 +335,7 @@ struct SimtTile {
         T z[C], p[NP], ab[C], zb[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          z[c] = zsrc[(long long)(c * P + pg * TP + j) * w + u];
+          z[c] = zz[c][j];
           ab[c] = abv[c][j];
         }
         tanh_derivs<T, NP>(z[0], p);

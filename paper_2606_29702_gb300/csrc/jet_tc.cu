@@ -44,10 +44,6 @@ struct TcPlan {
   CUtensorMap wmap, wlmap, wlomap;
 };
 
-struct TcBatch {
-  int dummy;
-};
-
 }  // namespace jet
 
 namespace {
@@ -203,7 +199,8 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   // TMEM <= 512 columns per SM
   int best_score = -1;
   TcPlan best = *t;
-  for (int P = 8; P <= 64; P += 8) {
+  const int p8 = JET_FLAG_TILE_GET(flags);
+  for (int P = p8 ? 8 * p8 : 8; P <= (p8 ? 8 * p8 : 64); P += 8) {
     TcPlan c = *t;
     c.P = P;
     c.cols = C * P;
@@ -212,7 +209,7 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
     c.top_cols = ntop * P;
     if (c.split3 && c.top_cols % 16) continue;
     const size_t sm = carve(c, C, p->n_out, p->d) + 1024;
-    if (sm > 220 * 1024) continue;
+    if (sm > 208 * 1024) continue;  // + ~17 KB of static shared memory per CTA
     const int NB = c.H == 2 ? 128 : w;
     c.r0w = std::max(c.cols_pad, NB);
     c.r1w = c.cols_pad;
@@ -222,8 +219,9 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
     if (tm > 512) continue;
     c.tmem_cols = tm;
     const int by_tmem = 512 / tm;
-    const int by_smem = (int)((228 * 1024) / (sm + 1024));
-    c.ctas_per_sm = std::max(1, std::min(by_tmem, by_smem));
+    int by_occ = 0;  // registers and shared memory
+    if (tc_occupancy(p->cls, sm, &by_occ) != cudaSuccess || by_occ < 1) continue;
+    c.ctas_per_sm = std::max(1, std::min(by_tmem, by_occ));
     const int score = P * c.ctas_per_sm;
     if (score > best_score) {
       best_score = score;
@@ -484,15 +482,205 @@ jet_status tc_train_step(jet_plan_s* p, TcPlan* t, void* params, void* m, void* 
   return e == cudaSuccess ? JET_OK : tcuda(e, "reduce/adam");
 }
 
-jet_status tc_batch_create(const std::vector<jet_plan_s*>&, TcBatch** out) {
+// ------------------------------------------------------------------ batches
+// Many plans (same channel set, any widths/depths/point counts) run as one
+// persistent launch of the fused kernel over a cost-ordered list of
+// (instance, chunk of tiles) items; every instance keeps its own tile size,
+// BF16 weight copies and TMA tensor maps.
+
+namespace jet {
+struct TcBatch {
+  int n = 0, cls = 0, grid = 0, tmem_cols = 0, max_chunks = 16, max_items = 0, n_items = 0;
+  size_t smem = 0;
+  TcInst* d_insts = nullptr;
+  TcInst* h_insts = nullptr;
+  int* d_items = nullptr;
+  int* h_items = nullptr;
+  ReduceJob* d_jobs = nullptr;
+  ReduceJob* h_jobs = nullptr;
+  double* grad_slices = nullptr;
+  double* loss_slices = nullptr;
+  std::vector<long long> slice_off;
+  unsigned char* scratch = nullptr;
+  long long scratch_stride = 0;
+  int* err = nullptr;
+  cudaEvent_t copied = nullptr;  // descriptor upload of the previous call
+  bool have_prev = false;
+};
+}  // namespace jet
+
+jet_status tc_batch_create(const std::vector<jet_plan_s*>& plans, TcBatch** out) {
   *out = nullptr;
-  return tfail(JET_ERR_UNSUPPORTED, "batched tensor-core launches are not provided by this build yet");
+  TcBatch* b = new TcBatch();
+  b->n = (int)plans.size();
+  b->cls = plans[0]->cls;
+  long long slices = 0;
+  for (jet_plan_s* p : plans) {
+    TcPlan* t = p->tcp;
+    b->smem = std::max(b->smem, t->smem);
+    b->tmem_cols = std::max(b->tmem_cols, t->tmem_cols);
+    b->scratch_stride = std::max(b->scratch_stride, t->scratch_stride);
+    b->slice_off.push_back(slices);
+    slices += (long long)b->max_chunks * p->n_params;
+  }
+  int dev = 0, sms = 0, occ = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = tc_occupancy(b->cls, b->smem, &occ);
+  if (e != cudaSuccess || occ < 1) {
+    delete b;
+    return e != cudaSuccess ? tcuda(e, "batch occupancy") : tfail(JET_ERR_UNSUPPORTED, "batch tile does not fit");
+  }
+  b->grid = sms * std::max(1, std::min(occ, 512 / b->tmem_cols));
+  b->max_items = b->n * b->max_chunks;
+  e = cudaMalloc((void**)&b->d_insts, sizeof(TcInst) * b->n);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_insts, sizeof(TcInst) * b->n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, sizeof(int) * 2 * b->max_items);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_items, sizeof(int) * 2 * b->max_items);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_jobs, sizeof(ReduceJob) * b->n);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_jobs, sizeof(ReduceJob) * b->n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->grad_slices, sizeof(double) * std::max<long long>(slices, 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->loss_slices, sizeof(double) * b->max_items);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->scratch, (size_t)b->grid * std::max<long long>(b->scratch_stride, 16));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    tc_batch_destroy(b);
+    return tcuda(e, "batch workspace");
+  }
+  memset(b->h_insts, 0, sizeof(TcInst) * b->n);
+  *out = b;
+  return JET_OK;
 }
 
-void tc_batch_destroy(TcBatch* b) { delete b; }
+void tc_batch_destroy(TcBatch* b) {
+  if (!b) return;
+  cudaFree(b->d_insts);
+  cudaFreeHost(b->h_insts);
+  cudaFree(b->d_items);
+  cudaFreeHost(b->h_items);
+  cudaFree(b->d_jobs);
+  cudaFreeHost(b->h_jobs);
+  cudaFree(b->grad_slices);
+  cudaFree(b->loss_slices);
+  cudaFree(b->scratch);
+  cudaFree(b->err);
+  if (b->copied) cudaEventDestroy(b->copied);
+  delete b;
+}
 
-jet_status tc_batch_run(TcBatch*, const std::vector<jet_plan_s*>&, const void* const*, void* const*, void* const*,
-                        long long, float, const void* const*, const int64_t*, const void* const*, void* const*,
-                        double*, bool, cudaStream_t) {
-  return tfail(JET_ERR_UNSUPPORTED, "batched tensor-core launches are not provided by this build yet");
+jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, const void* const* params, void* const* m,
+                        void* const* v, long long step, float lr, const void* const* X, const int64_t* N,
+                        const void* const* source, void* const* grad_out, double* loss_out, bool adam,
+                        cudaStream_t s) {
+  TcBatch* b = bb;
+  const int n = b->n;
+  long long total_tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    if (N[i] < 1) return tfail(JET_ERR_INVALID, "batched calls need N >= 1 for every instance");
+    if (!params[i] || !X[i]) return tfail(JET_ERR_INVALID, "NULL params or X in batch");
+    if (plans[i]->has_source != (source && source[i])) return tfail(JET_ERR_INVALID, "source does not match spec");
+    total_tiles += (N[i] + plans[i]->tcp->P - 1) / plans[i]->tcp->P;
+  }
+  for (int i = 0; i < n; ++i) {
+    jet_status st = prep(plans[i], plans[i]->tcp, params[i], s);
+    if (st != JET_OK) return st;
+  }
+  // work list: about four items per CTA, cost-ordered, largest first
+  const long long target = std::max<long long>(1, (total_tiles + 4LL * b->grid - 1) / (4LL * b->grid));
+  std::vector<TcInst> insts(n);
+  std::vector<std::pair<double, int>> cost;
+  std::vector<int> inst_of;
+  int base = 0;
+  for (int i = 0; i < n; ++i) {
+    jet_plan_s* p = plans[i];
+    TcPlan* t = p->tcp;
+    TcInst& I = insts[i];
+    fill_tc(p, t, params[i], X[i], N[i], source ? source[i] : nullptr, nullptr, I);
+    const long long chunks = std::min<long long>(b->max_chunks, std::max<long long>(1, (I.n_tiles + target - 1) / target));
+    I.tiles_per_chunk = (int)((I.n_tiles + chunks - 1) / chunks);
+    I.n_chunks = (int)((I.n_tiles + I.tiles_per_chunk - 1) / I.tiles_per_chunk);
+    I.chunk_base = base;
+    I.grad_slices = b->grad_slices + b->slice_off[i];
+    I.loss_slices = b->loss_slices + (long long)i * b->max_chunks;
+    I.scratch = b->scratch;
+    I.scratch_stride = b->scratch_stride;
+    double per_tile = (double)(p->L - 1) * t->w * t->w * t->cols_pad + 2000.0 * t->w * t->P * (p->L - 1);
+    for (int c = 0; c < I.n_chunks; ++c) {
+      const long long t0 = (long long)c * I.tiles_per_chunk;
+      const long long nt = std::min<long long>(I.n_tiles, t0 + I.tiles_per_chunk) - t0;
+      cost.push_back({per_tile * (double)nt, base + c});
+      inst_of.push_back(i);
+    }
+    base += I.n_chunks;
+  }
+  std::stable_sort(cost.begin(), cost.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+    return x.first > y.first;
+  });
+  const bool capturing = [&] {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    return cs != cudaStreamCaptureStatusNone;
+  }();
+  // upload the descriptors only when they changed; wait for the previous
+  // upload to have read the staging buffers before rewriting them
+  bool same = b->have_prev && b->n_items == base && memcmp(b->h_insts, insts.data(), sizeof(TcInst) * n) == 0;
+  if (same)
+    for (int k = 0; k < base && same; ++k) same = b->h_items[k] == cost[k].second && b->h_items[base + k] == inst_of[k];
+  if (!same) {
+    if (b->have_prev && !capturing) cudaEventSynchronize(b->copied);
+    memcpy(b->h_insts, insts.data(), sizeof(TcInst) * n);
+    for (int k = 0; k < base; ++k) {
+      b->h_items[k] = cost[k].second;
+      b->h_items[base + k] = inst_of[k];
+    }
+    b->n_items = base;
+    cudaError_t e = cudaMemcpyAsync(b->d_insts, b->h_insts, sizeof(TcInst) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_items, b->h_items, sizeof(int) * 2 * base, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !capturing) e = cudaEventRecord(b->copied, s);
+    if (e != cudaSuccess) return tcuda(e, "batch descriptor upload");
+    b->have_prev = b->have_prev || !capturing;
+  }
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  a.mode = MODE_FWD_BWD;
+  a.n_items = base;
+  a.insts = b->d_insts;
+  a.item_inst = b->d_items;
+  a.err = b->err;
+  a.tmem_cols = b->tmem_cols;
+  cudaError_t e = tc_launch(b->cls, a, std::min(b->grid, base), b->smem, s);
+  if (e != cudaSuccess) return tcuda(e, "batched tc kernel launch");
+  long long maxp = 0;
+  bool jobs_same = !capturing;
+  for (int i = 0; i < n; ++i) {
+    ReduceJob j;
+    memset(&j, 0, sizeof(j));
+    j.grad_slices = insts[i].grad_slices;
+    j.loss_slices = insts[i].loss_slices;
+    j.n_chunks = insts[i].n_chunks;
+    j.n_params = plans[i]->n_params;
+    j.inv_N = insts[i].inv_N;
+    j.grad_out = adam ? nullptr : grad_out[i];
+    j.loss_out = loss_out ? loss_out + i : nullptr;
+    if (adam) {
+      j.params = const_cast<void*>(params[i]);
+      j.m = m[i];
+      j.v = v[i];
+    }
+    if (jobs_same && memcmp(&b->h_jobs[i], &j, sizeof(j)) != 0) {
+      jobs_same = false;
+      if (b->have_prev && !capturing) cudaEventSynchronize(b->copied);
+    }
+    if (!jobs_same || capturing) b->h_jobs[i] = j;
+    maxp = std::max(maxp, j.n_params);
+  }
+  if (!jobs_same || capturing) {
+    e = cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(ReduceJob) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !capturing) e = cudaEventRecord(b->copied, s);
+    if (e != cudaSuccess) return tcuda(e, "batch job upload");
+  }
+  e = launch_reduce(b->d_jobs, b->h_jobs[0], n, maxp, false, adam, step, lr, s);
+  return e == cudaSuccess ? JET_OK : tcuda(e, "batch reduce");
 }

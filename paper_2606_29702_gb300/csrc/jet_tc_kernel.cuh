@@ -41,7 +41,30 @@
 
 namespace jet {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 512;
+constexpr int kTcWG = 4;  // warpgroups; each covers the four TMEM lane quadrants
+
+// p[k] = tanh^(k)(z) for the tensor-core epilogue.  q = 1 - tanh|z| =
+// 2 / (exp(2|z|) + 1) is formed with the approximate exp2 and reciprocal
+// units; tanh z = sign(z) (1 - q) and s = 1 - tanh^2 z = q (2 - q), which keeps
+// s accurate in relative terms where |z| is large (no 1 - a^2 cancellation).
+template <int NP>
+__device__ __forceinline__ void tanh_derivs_fast(float z, float* p) {
+  const float az = fabsf(z);
+  float e, r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(az * 2.8853900817779268f));  // exp(2|z|)
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
+  const float q = 2.0f * r;
+  const float a = copysignf(1.0f - q, z);
+  const float s = q * (2.0f - q);
+  const float a2 = a * a;
+  p[0] = a;
+  if (NP > 1) p[1] = s;
+  if (NP > 2) p[2] = -2.0f * a * s;
+  if (NP > 3) p[3] = s * (6.0f * a2 - 2.0f);
+  if (NP > 4) p[4] = 8.0f * a * s * (2.0f - 3.0f * a2);
+  if (NP > 5) p[5] = 8.0f * s * (15.0f * a2 * a2 - 15.0f * a2 + 2.0f);
+}
 
 struct alignas(64) TcInst {
   CUtensorMap wmap;    // hidden weights bf16 [L-2][w][w]: dims (in, out, layer), box (64, R_W, 1)
@@ -85,8 +108,8 @@ struct TcTile {
   static constexpr int C = Cls::C;
   static constexpr int NP = Cls::NP;
   static constexpr int TOP = Cls::TOP_BEGIN;
-  static constexpr int PPF = 4;                // points per epilogue pass (forward)
-  static constexpr int PPB = C >= 10 ? 2 : 4;  // points per epilogue pass (adjoint)
+  static constexpr int PPF = C >= 7 ? 2 : 4;   // points per epilogue pass (forward)
+  static constexpr int PPB = C >= 5 ? 2 : 4;   // points per epilogue pass (adjoint)
 
   const TcInst& I;
   unsigned char* sm;
@@ -98,7 +121,9 @@ struct TcTile {
   uint32_t tmem;
   uint32_t ph_tma, ph_mma, ph_ld;
   int tid, warp;
-  int R;  // rows of every operand buffer (128 * H)
+  int R;        // rows of every operand buffer (128 * H)
+  float* part;  // per-warpgroup partial sums [kTcWG][4][256]
+  int q, wg, ul;  // TMEM lane quadrant, warpgroup, unit within a 128-row half
 
   // column block of channel c: highest-order channels first
   static __device__ __forceinline__ int blk(int c) { return c >= TOP ? c - TOP : c + (C - TOP); }
@@ -110,7 +135,8 @@ struct TcTile {
   __device__ unsigned char* ALO(int i) const { return sm + (i ? I.o_alo1 : I.o_alo0); }
   __device__ uint32_t R0(int h) const { return tmem + (uint32_t)(h * I.r0w); }
   __device__ uint32_t R1(int h) const { return tmem + (uint32_t)(I.H * I.r0w + h * I.r1w); }
-  __device__ uint32_t lane_base() const { return (uint32_t)(warp * 32) << 16; }
+  __device__ uint32_t lane_base() const { return (uint32_t)(q * 32) << 16; }
+  __device__ float& PART(int w, int k, int u) const { return part[(w * 4 + k) * 256 + u]; }
 
   __device__ bool wait(uint64_t* bar, uint32_t& ph, int code) {
     const bool ok = tc::mbar_wait(bar, ph & 1u, abort_f, err, code);
@@ -241,12 +267,12 @@ struct TcTile {
   __device__ void layer1_fwd(int out_buf) {
     const float* Pm = I.params;
     for (int h = 0; h < I.H; ++h) {
-      const int u = h * 128 + tid;
+      const int u = h * 128 + ul;
       if (u >= I.w) continue;
       float w1[3] = {0.f, 0.f, 0.f};
       for (int i = 0; i < I.d; ++i) w1[i] = Pm[I.off_W[0] + u * I.d + i];
       const float b1 = Pm[I.off_b[0] + u];
-      for (int g = 0; g < I.P; g += PPF) {
+      for (int g = wg * PPF; g < I.P; g += kTcWG * PPF) {
         float av[C][PPF];
 #pragma unroll
         for (int j = 0; j < PPF; ++j) {
@@ -261,7 +287,7 @@ struct TcTile {
             const int fo = Cls::first_order(i);
             if (fo >= 0) z[fo] = w1[i];
           }
-          tanh_derivs<float, NP>(z[0], p);
+          tanh_derivs_fast<NP>(z[0], p);
           Cls::compose(z, p, a);
 #pragma unroll
           for (int c = 0; c < C; ++c) av[c][j] = a[c];
@@ -278,10 +304,10 @@ struct TcTile {
   // a^l = compose(D[R0] + b^l) -> ACT(out_buf)
   __device__ void hidden_epilogue(int l, int out_buf) {
     for (int h = 0; h < I.H; ++h) {
-      const int u = h * 128 + tid;
-      if (h * 128 + warp * 32 >= I.w) continue;  // warp-uniform
+      const int u = h * 128 + ul;
+      if (h * 128 + q * 32 >= I.w) continue;  // warp-uniform
       const float bu = I.params[I.off_b[l - 1] + u];
-      for (int g = 0; g < I.P; g += PPF) {
+      for (int g = wg * PPF; g < I.P; g += kTcWG * PPF) {
         float zv[C][PPF];
 #pragma unroll
         for (int c = 0; c < C; ++c) tc::tmem_ld<PPF>(R0(h) + lane_base() + (uint32_t)(blk(c) * I.P + g), zv[c]);
@@ -293,7 +319,7 @@ struct TcTile {
 #pragma unroll
           for (int c = 0; c < C; ++c) z[c] = zv[c][j];
           z[0] += bu;
-          tanh_derivs<float, NP>(z[0], p);
+          tanh_derivs_fast<NP>(z[0], p);
           Cls::compose(z, p, a);
 #pragma unroll
           for (int c = 0; c < C; ++c) av[c][j] = a[c];
@@ -363,24 +389,41 @@ struct TcTile {
 
   // ------------------------------------------------------------ backward pieces
   // dW^L[o][k] += sum_cols ub[o][col] a^{L-1}[k][col]; db^L[o] += sum_n ub[o][0][n]
-  __device__ void out_grads(int a_buf, double* g) {
+  // (warpgroups split the channel blocks; partials go to PART and are summed
+  // in a fixed order by out_grads_flush after a barrier)
+  __device__ void out_grads(int a_buf) {
     const float* ub = UB();
-    const int P = I.P, L = I.L;
+    const int P = I.P;
     for (int h = 0; h < I.H; ++h) {
-      const int k = h * 128 + tid;
+      const int k = h * 128 + ul;
       if (k >= I.w) continue;
       float acc[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
-      for (int c = 0; c < C; ++c)
-        for (int q = 0; q < P; q += 8) {
-          const int col = blk(c) * P + q;
+      for (int c = wg; c < C; c += kTcWG)
+        for (int q8 = 0; q8 < P; q8 += 8) {
+          const int col = blk(c) * P + q8;
           const uint4 raw = *reinterpret_cast<const uint4*>(ACT(a_buf) + tc::swz_off(k, col, R));
           const __nv_bfloat16* bv = reinterpret_cast<const __nv_bfloat16*>(&raw);
           for (int o = 0; o < I.n_out; ++o)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[o] = fmaf(__bfloat162float(bv[j]), ub[(o * C + c) * P + q + j], acc[o]);
+            for (int j = 0; j < 8; ++j) acc[o] = fmaf(__bfloat162float(bv[j]), ub[(o * C + c) * P + q8 + j], acc[o]);
         }
-      for (int o = 0; o < I.n_out; ++o) tc::red_add_f64(g + I.off_W[L - 1] + (long long)o * I.w + k, (double)acc[o]);
+      for (int o = 0; o < I.n_out; ++o) PART(wg, o, k) = acc[o];
     }
+  }
+
+  __device__ void out_grads_flush(double* g) {
+    const float* ub = UB();
+    const int P = I.P, L = I.L;
+    if (wg == 0)
+      for (int h = 0; h < I.H; ++h) {
+        const int k = h * 128 + ul;
+        if (k >= I.w) continue;
+        for (int o = 0; o < I.n_out; ++o) {
+          double s = 0.0;
+          for (int w2 = 0; w2 < kTcWG; ++w2) s += (double)PART(w2, o, k);
+          tc::red_add_f64(g + I.off_W[L - 1] + (long long)o * I.w + k, s);
+        }
+      }
     if (tid < I.n_out) {
       float s = 0.f;
       for (int n = 0; n < P; ++n) s += ub[(tid * C + 0) * P + n];
@@ -388,19 +431,31 @@ struct TcTile {
     }
   }
 
+  // sum of per-warpgroup partials in slot k of PART -> FP64 slice at dst[u]
+  __device__ void part_flush(int k, double* dst, int stride) {
+    if (wg != 0) return;
+    for (int h = 0; h < I.H; ++h) {
+      const int u = h * 128 + ul;
+      if (u >= I.w) continue;
+      double s = 0.0;
+      for (int w2 = 0; w2 < kTcWG; ++w2) s += (double)PART(w2, k, u);
+      tc::red_add_f64(dst + (long long)u * stride, s);
+    }
+  }
+
   // Zbar^l = (d compose/dz)^T Abar^l -> ACT(z_buf); db^l += sum_n Zbar_0
-  __device__ void adjoint_epilogue(int l, int z_buf, bool abar_from_ub, double* g) {
+  __device__ void adjoint_epilogue(int l, int z_buf, bool abar_from_ub) {
     const float* ub = UB();
     const int P = I.P;
     for (int h = 0; h < I.H; ++h) {
-      const int u = h * 128 + tid;
-      if (h * 128 + warp * 32 >= I.w) continue;
+      const int u = h * 128 + ul;
+      if (h * 128 + q * 32 >= I.w) continue;
       const float bu = I.params[I.off_b[l - 1] + u];
       float wl[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
       if (abar_from_ub)
         for (int o = 0; o < I.n_out; ++o) wl[o] = I.params[I.off_W[I.L - 1] + (long long)o * I.w + u];
       float gb = 0.f;
-      for (int q = 0; q < P; q += PPB) {
+      for (int q = wg * PPB; q < P; q += kTcWG * PPB) {
         float zv[C][PPB], abv[C][PPB];
 #pragma unroll
         for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R0(h) + lane_base() + (uint32_t)(blk(c) * P + q), zv[c]);
@@ -429,7 +484,7 @@ struct TcTile {
             ab[c] = abv[c][j];
           }
           z[0] += bu;
-          tanh_derivs<float, NP>(z[0], p);
+          tanh_derivs_fast<NP>(z[0], p);
           Cls::adjoint(z, p, ab, zb);
 #pragma unroll
           for (int c = 0; c < C; ++c) zbv[c][j] = zb[c];
@@ -438,7 +493,7 @@ struct TcTile {
 #pragma unroll
         for (int c = 0; c < C; ++c) st_bf16<PPB>(ACT(z_buf), u, blk(c) * P + q, zbv[c]);
       }
-      if (u < I.w) tc::red_add_f64(g + I.off_b[l - 1] + u, (double)gb);
+      PART(wg, 0, u) = gb;
     }
   }
 
@@ -446,9 +501,9 @@ struct TcTile {
   __device__ void flush_wgrad(int l, int nb, int NB, double* g) {
     double* gW = g + I.off_W[l - 1];
     for (int h = 0; h < I.H; ++h) {
-      if (h * 128 + warp * 32 >= I.w) continue;
-      const int j = h * 128 + tid;
-      for (int k0 = 0; k0 < NB; k0 += 8) {
+      if (h * 128 + q * 32 >= I.w) continue;
+      const int j = h * 128 + ul;
+      for (int k0 = wg * 8; k0 < NB; k0 += kTcWG * 8) {
         float v[8];
         tc::tmem_ld8(R0(h) + lane_base() + (uint32_t)k0, v);
         tc::tmem_wait_ld();
@@ -461,13 +516,13 @@ struct TcTile {
   }
 
   // layer-1 backward with z^1 recomputed from the points
-  __device__ void layer1_bwd(bool abar_from_ub, double* g) {
+  __device__ void layer1_bwd(bool abar_from_ub) {
     const float* Pm = I.params;
     const float* ub = UB();
     const int P = I.P;
     for (int h = 0; h < I.H; ++h) {
-      const int u = h * 128 + tid;
-      if (h * 128 + warp * 32 >= I.w) continue;
+      const int u = h * 128 + ul;
+      if (h * 128 + q * 32 >= I.w) continue;
       float w1[3] = {0.f, 0.f, 0.f};
       for (int i = 0; i < I.d; ++i) w1[i] = Pm[I.off_W[0] + u * I.d + i];
       const float b1 = Pm[I.off_b[0] + u];
@@ -475,7 +530,7 @@ struct TcTile {
       if (abar_from_ub)
         for (int o = 0; o < I.n_out; ++o) wl[o] = Pm[I.off_W[I.L - 1] + (long long)o * I.w + u];
       float gw[3] = {0.f, 0.f, 0.f}, gb = 0.f;
-      for (int q = 0; q < P; q += PPB) {
+      for (int q = wg * PPB; q < P; q += kTcWG * PPB) {
         float abv[C][PPB];
         if (!abar_from_ub) {
 #pragma unroll
@@ -507,7 +562,7 @@ struct TcTile {
             const int fo = Cls::first_order(i);
             if (fo >= 0) z[fo] = w1[i];
           }
-          tanh_derivs<float, NP>(z[0], p);
+          tanh_derivs_fast<NP>(z[0], p);
           Cls::adjoint(z, p, ab, zb);
           gb += zb[0];
           for (int i = 0; i < I.d; ++i) gw[i] = fmaf(zb[0], XS()[(q + j) * I.d + i], gw[i]);
@@ -518,9 +573,14 @@ struct TcTile {
           }
         }
       }
-      for (int i = 0; i < I.d; ++i) tc::red_add_f64(g + I.off_W[0] + (long long)u * I.d + i, (double)gw[i]);
-      tc::red_add_f64(g + I.off_b[0] + u, (double)gb);
+      for (int i = 0; i < 3; ++i) PART(wg, i, u) = gw[i];
+      PART(wg, 3, u) = gb;
     }
+  }
+
+  __device__ void layer1_flush(double* g) {
+    for (int i = 0; i < I.d; ++i) part_flush(i, g + I.off_W[0] + i, I.d);
+    part_flush(3, g + I.off_b[0], 1);
   }
 
   // ------------------------------------------------------------ one tile
@@ -595,8 +655,9 @@ struct TcTile {
     __syncthreads();
     if (!bwd || *abort_f) return loss;
     // ---- backward
-    out_grads(cur, g);
+    out_grads(cur);
     __syncthreads();
+    out_grads_flush(g);
     const int zb = cur, ain = cur ^ 1;
     for (int l = L - 1; l >= 2; --l) {
       if (l < L - 1) {
@@ -620,9 +681,10 @@ struct TcTile {
       } else {
         if (!wait(bar_tma, ph_tma, 63)) break;  // W^{L-1} for the data gradient
       }
-      adjoint_epilogue(l, zb, l == L - 1, g);
+      adjoint_epilogue(l, zb, l == L - 1);
       tc::fence_proxy_async_smem();
       sync();
+      part_flush(0, g + I.off_b[l - 1], 1);  // bias gradient of layer l
       const int NB = I.H == 2 ? 128 : I.w;
       const int nblk = I.w / NB;
       if (tid == 0) {
@@ -645,8 +707,10 @@ struct TcTile {
       }
       sync();
     }
-    if (!*abort_f) layer1_bwd(L == 2, g);
+    if (!*abort_f) layer1_bwd(L == 2);
     sync();
+    if (!*abort_f) layer1_flush(g);
+    __syncthreads();
     return loss;
   }
 };
@@ -658,6 +722,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
   __shared__ uint32_t tmem_s;
   __shared__ volatile int abort_s;
   __shared__ double red_s[kTcThreads / 32];
+  __shared__ float part_s[kTcWG * 4 * 256];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
@@ -704,8 +769,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
       __syncthreads();
       prev_inst = ii;
     }
-    TcTile<Cls> T{I, sm, &bars[0], &bars[1], &bars[2], &abort_s, args.err, tmem_s, ph_tma, ph_mma, ph_ld, tid, warp,
-                  128 * I.H};
+    TcTile<Cls> T{I,   sm,      &bars[0], &bars[1], &bars[2], &abort_s,      args.err, tmem_s, ph_tma,
+                  ph_mma, ph_ld, tid,      warp,     128 * I.H, &part_s[0], warp & 3, warp >> 2, tid & 127};
     const bool bwd = args.mode != MODE_FWD;
     double* g = bwd ? I.grad_slices + (long long)chunk * I.n_params : nullptr;
     if (bwd)

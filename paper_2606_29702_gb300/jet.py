@@ -133,8 +133,10 @@ def _spec_struct(spec):
 class Plan:
     """A libjet plan: one residual on one network shape at one precision."""
 
-    def __init__(self, spec, widths, precision="fp32", needed=None, mem_budget=0, store=False, auto_close=True):
+    def __init__(self, spec, widths, precision="fp32", needed=None, mem_budget=0, store=False, auto_close=True,
+                 tile=None):
         L = load()
+        self.tile = tile
         self.spec = spec
         self.widths = list(widths)
         self.precision = precision
@@ -146,6 +148,10 @@ class Plan:
                 nd[i].alpha[j] = k
         w = (ctypes.c_int32 * len(widths))(*widths)
         flags = (FLAG_AUTO_CLOSE if auto_close else 0) | (FLAG_STORE if store else 0)
+        if tile:
+            if tile % 8 or not 8 <= tile <= 2040:
+                raise ValueError("tile must be a multiple of 8 in [8, 2040]")
+            flags |= (tile // 8) << 8
         h = ctypes.c_void_p()
         _check(L.jet_plan_create(ctypes.byref(h), ctypes.byref(s), spec.d_in, len(widths) - 1, w, len(needed), nd,
                                  PRECISIONS[precision], int(mem_budget), flags))
