@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "residual+param-grad collocation pts/s on 1 GB300; TC roofline %; rel err vs FP64"
 UNIT = "points/s"
 L2_BYTES = 129 * 1024 * 1024
+STORE_BUDGET = 96 << 30  # HBM the tensor-core forms may use for the weight-gradient store
 
 
 def parse():
@@ -287,7 +288,11 @@ def time_form(spec, form, X_host, steps, warmup, flush, want_kernel=False, e2e=F
     from paper_2606_29702_gb300 import jet, specs
     from paper_2606_29702_gb300 import workloads as wl
     sp = specs.by_name(spec["family"], **spec["coefs"])
-    plan = jet.Plan(sp, spec["widths"], form)
+    # wide tensor-core layers keep layer inputs and adjoints in HBM (store mode,
+    # up to STORE_BUDGET bytes) so that the weight gradients run as one GEMM per
+    # layer; narrower ones flush per tile (the faster choice measured there)
+    store = form in ("bf16", "bf16x3", "tf32") and max(spec["widths"][1:-1]) >= 256
+    plan = jet.Plan(sp, spec["widths"], form, store=store, mem_budget=STORE_BUDGET if store else 0)
     dt = plan.dtype
     dev = torch.device("cuda")
     layers = wl.xavier_layers(spec["widths"], spec["seed_par"])

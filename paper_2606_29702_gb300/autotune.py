@@ -60,35 +60,63 @@ def _time_plan(plan, params, X, source, reps):
     return a.elapsed_time(b) / reps
 
 
+STORE_BUDGET = 96 << 30
+
+
 def tune(spec, widths, precision, params, X, source=None, candidates=DEFAULT_CANDIDATES, reps=3, path=None,
-         timer=None):
-    """Time every candidate tile size; cache and return (best_tile, {tile: ms})."""
+         timer=None, schedules=None):
+    """Time every (tile size, weight-gradient schedule) pair; cache and return
+    (best_tile, {tile: ms}) -- the ms of each tile's faster schedule.
+
+    Schedules of the tensor-core forms: "tile" (weight gradient flushed per
+    tile, bounded memory) and "store" (layer inputs and adjoints in HBM, one
+    weight-gradient GEMM per layer); the SIMT forms have one schedule.
+    """
     timer = timer or _time_plan
-    results = {}
+    if schedules is None:
+        schedules = ("tile", "store") if precision in ("bf16", "bf16x3", "tf32") else ("tile",)
+    results, sched = {}, {}
     for P in candidates:
-        try:
-            plan = jet.Plan(spec, widths, precision, tile=P)
-        except jet.JetError:
-            continue  # does not fit shared memory / TMEM for this shape
-        try:
-            results[P] = float(timer(plan, params, X, source, reps))
-        finally:
-            plan.close()
+        for sc in schedules:
+            kw = dict(store=True, mem_budget=STORE_BUDGET) if sc == "store" else {}
+            try:
+                plan = jet.Plan(spec, widths, precision, tile=P, **kw)
+            except jet.JetError:
+                continue  # does not fit shared memory / TMEM for this shape
+            try:
+                ms = float(timer(plan, params, X, source, reps))
+            finally:
+                plan.close()
+            if P not in results or ms < results[P]:
+                results[P], sched[P] = ms, sc
     if not results:
         raise RuntimeError("no candidate tile size fits this shape")
     best = min(results, key=lambda k: (results[k], k))
     cache = load_cache(path)
-    cache[shape_key(spec, widths, precision)] = {"tile": int(best), "ms": {str(k): v for k, v in results.items()}}
+    cache[shape_key(spec, widths, precision)] = {"tile": int(best), "schedule": sched[best],
+                                                 "ms": {str(k): v for k, v in results.items()}}
     save_cache(cache, path)
     return best, results
 
 
+def tuned(spec, widths, precision, path=None):
+    """Cached (tile, schedule) for the shape, or None."""
+    e = load_cache(path).get(shape_key(spec, widths, precision))
+    return None if e is None else (int(e["tile"]), e.get("schedule", "tile"))
+
+
 def tuned_tile(spec, widths, precision, path=None):
     """Cached tile size for the shape, or None."""
-    e = load_cache(path).get(shape_key(spec, widths, precision))
-    return None if e is None else int(e["tile"])
+    t = tuned(spec, widths, precision, path)
+    return None if t is None else t[0]
 
 
 def plan(spec, widths, precision, path=None, **kw):
-    """A plan that uses the cached tile size of its shape when there is one."""
-    return jet.Plan(spec, widths, precision, tile=tuned_tile(spec, widths, precision, path), **kw)
+    """A plan that uses the cached tile size and schedule of its shape when there is one."""
+    t = tuned(spec, widths, precision, path)
+    if t is None:
+        return jet.Plan(spec, widths, precision, **kw)
+    if t[1] == "store":
+        kw.setdefault("store", True)
+        kw.setdefault("mem_budget", STORE_BUDGET)
+    return jet.Plan(spec, widths, precision, tile=t[0], **kw)

@@ -91,6 +91,7 @@ struct ReduceJob {
   const double* grad_slices;
   const double* loss_slices;
   int n_chunks;
+  int grad_chunks;    // gradient slices to sum (0: n_chunks; 1: one shared accumulator)
   long long n_params;
   double inv_N;
   void* grad_out;     // value type T or null

@@ -43,7 +43,8 @@ __global__ void reduce_kernel(const __grid_constant__ ReduceJob job0, const Redu
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < J.n_params;
        p += (long long)gridDim.x * blockDim.x) {
     double g = 0.0;
-    for (int c = 0; c < J.n_chunks; ++c) g += J.grad_slices[(long long)c * J.n_params + p];
+    const int gc = J.grad_chunks > 0 ? J.grad_chunks : J.n_chunks;
+    for (int c = 0; c < gc; ++c) g += J.grad_slices[(long long)c * J.n_params + p];
     if (J.grad_out) reinterpret_cast<T*>(J.grad_out)[p] = (T)g;
     if (ADAM) {
       T* th = reinterpret_cast<T*>(J.params);

@@ -42,7 +42,164 @@ struct TcPlan {
   cudaEvent_t err_ev = nullptr;
   size_t ws_bytes = 0;
   CUtensorMap wmap, wlmap, wlomap;
+  // per-chunk FP64 gradient slices when they fit in a share of L2, else one
+  // accumulator that every chunk adds into (atomic order not fixed)
+  bool shared_acc = false;
+  // store mode of the weight gradient (JET_FLAG_STORE with a memory budget):
+  // per tile A^1..A^{L-2} and Zbar^2..Zbar^{L-1} in HBM, reduced by the
+  // weight-gradient GEMM kernel into one FP64 partial per work item
+  unsigned char* wstore = nullptr;
+  long long wstore_tile_stride = 0, wstore_tiles = 0;
+  size_t wstore_budget = 0;  // grown on demand up to this many bytes
+  double* wg_out = nullptr;  // [max_items][w*w]
+  int wg_max_items = 0, wg_sms = 0;
 };
+
+// budget of the per-chunk gradient slices (they are updated once per tile)
+constexpr double kSliceBudgetBytes = 32.0 * 1024 * 1024;
+
+// ------------------------------------------------------------------ weight-gradient GEMM
+// Wbar^l = sum over the tiles of a K range of Zbar^l A^{l-1}^T, both operands
+// read from the store in the fused kernel's swizzled layout, 64 columns
+// (one layout chunk) per pipeline stage; the accumulator stays in TMEM for
+// the whole range and is written once, in FP64, to the item's partial.
+struct WgArgs {
+  const unsigned char* wstore;
+  long long tile_stride;  // bytes per tile in the store
+  long long a_slot;       // bytes between consecutive A^l copies
+  long long z_off;        // offset of Zbar^2 within a tile
+  int act_bytes, chunk_bytes, ach, stages;
+  int L, w, H;
+  long long n_tiles;
+  int items_per_layer, n_items;
+  long long tiles_per_item;
+  double* out;
+  int* err;
+  int tmem_cols;
+};
+
+constexpr int kWgThreads = 128;
+constexpr int kWgMaxStages = 4;
+
+__global__ void __launch_bounds__(kWgThreads, 1) wgrad_kernel(const __grid_constant__ WgArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t full[kWgMaxStages], empty[kWgMaxStages], done;
+  __shared__ uint32_t tmem_s;
+  __shared__ volatile int abort_s;
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    abort_s = 0;
+    for (int s = 0; s < kWgMaxStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(&done, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_s, (uint32_t)a.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_s;
+  uint32_t fph[kWgMaxStages] = {0, 0, 0, 0}, eph[kWgMaxStages] = {0, 0, 0, 0}, dph = 0;
+  const int ww = a.w * a.w;
+  const uint32_t id = tc::idesc_bf16(128, a.w, 0, 0);
+  for (int item = blockIdx.x; item < a.n_items && !abort_s; item += gridDim.x) {
+    const int l = item / a.items_per_layer + 2;
+    const long long t0 = (long long)(item % a.items_per_layer) * a.tiles_per_item;
+    const long long t1 = t0 + a.tiles_per_item < a.n_tiles ? t0 + a.tiles_per_item : a.n_tiles;
+    const long long nch = t1 > t0 ? (t1 - t0) * a.ach : 0;
+    double* out = a.out + (long long)item * ww;
+    if (nch == 0) {
+      for (int i = tid; i < ww; i += kWgThreads) out[i] = 0.0;
+      continue;
+    }
+    if (tid == 0) {
+      bool pending[kWgMaxStages] = {false, false, false, false};
+      auto load = [&](long long i, int st) {
+        const long long t = t0 + i / a.ach;
+        const int cc = (int)(i % a.ach);
+        const unsigned char* base = a.wstore + t * a.tile_stride;
+        unsigned char* zs = sm + (size_t)st * 2 * a.chunk_bytes;
+        tc::mbar_arrive_expect_tx(&full[st], (uint32_t)(2 * a.chunk_bytes));
+        tc::bulk_g2s(zs, base + a.z_off + (long long)(l - 2) * a.act_bytes + (long long)cc * a.chunk_bytes,
+                     (uint32_t)a.chunk_bytes, &full[st]);
+        tc::bulk_g2s(zs + a.chunk_bytes, base + (long long)(l - 2) * a.a_slot + (long long)cc * a.chunk_bytes,
+                     (uint32_t)a.chunk_bytes, &full[st]);
+      };
+      const int S = a.stages;
+      for (long long i = 0; i < S && i < nch; ++i) load(i, (int)i);
+      for (long long i = 0; i < nch && !abort_s; ++i) {
+        const int st = (int)(i % S);
+        if (!tc::mbar_wait(&full[st], fph[st] & 1u, &abort_s, a.err, 71)) break;
+        ++fph[st];
+        tc::tc_fence_after();
+        const uint32_t zs = tc::smem_u32(sm + (size_t)st * 2 * a.chunk_bytes);
+        const uint32_t as = zs + (uint32_t)a.chunk_bytes;
+        for (int h = 0; h < a.H; ++h)
+          for (int s = 0; s < 4; ++s)
+            tc::mma_f16(tmem + (uint32_t)(h * a.w), tc::sdesc(zs + (uint32_t)h * 16384u + (uint32_t)s * 32u, 16, 1024),
+                        tc::sdesc(as + (uint32_t)s * 32u, 16, 1024), id, (i > 0 || s > 0) ? 1u : 0u);
+        tc::mma_commit(&empty[st]);
+        pending[st] = true;
+        if (i + S < nch) {
+          if (!tc::mbar_wait(&empty[st], eph[st] & 1u, &abort_s, a.err, 72)) break;
+          ++eph[st];
+          pending[st] = false;
+          load(i + S, st);
+        }
+      }
+      for (int st = 0; st < S; ++st)
+        if (pending[st]) {
+          tc::mbar_wait(&empty[st], eph[st] & 1u, &abort_s, a.err, 73);
+          ++eph[st];
+        }
+      tc::mma_commit(&done);
+    }
+    if (!tc::mbar_wait(&done, dph & 1u, &abort_s, a.err, 74)) break;
+    ++dph;
+    tc::tc_fence_after();
+    for (int h = 0; h < a.H; ++h) {
+      const int row = h * 128 + tid;
+      for (int k0 = 0; k0 < a.w; k0 += 8) {
+        float v[8];
+        tc::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * a.w + k0), v);
+        tc::tmem_wait_ld();
+        if (row < a.w)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) out[(long long)row * a.w + k0 + i] = (double)v[i];
+      }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+}
+
+// dst[off_W[l-1] + r] += sum over the items of layer l of out[item][r]
+struct OffWl {
+  long long v[kMaxLayers];
+};
+
+__global__ void wgrad_sum_kernel(const double* out, int L, int w, int ipl, OffWl offW, double* dst) {
+  const long long ww = (long long)w * w, total = (long long)(L - 2) * ww;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int li = (int)(e / ww);
+    const long long r = e % ww;
+    double s = 0.0;
+    for (int k = 0; k < ipl; ++k) s += out[((long long)li * ipl + k) * ww + r];
+    dst[offW.v[li + 1] + r] += s;
+  }
+}
 
 }  // namespace jet
 
@@ -249,7 +406,8 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   // workspace
   const long long nh = (long long)std::max(0, L - 2) * w * w, nl = (long long)p->n_out * w;
   size_t b_wh = std::max<long long>(nh, 1) * 2, b_wl = nl * 2, b_wlo = t->split3 ? b_wh : 0;
-  size_t b_gs = (size_t)t->grid * p->n_params * 8, b_ls = (size_t)t->grid * 8;
+  t->shared_acc = (double)t->grid * p->n_params * 8.0 > kSliceBudgetBytes;
+  size_t b_gs = (size_t)(t->shared_acc ? 1 : t->grid) * p->n_params * 8, b_ls = (size_t)t->grid * 8;
   size_t b_sc = (size_t)t->grid * std::max<long long>(t->scratch_stride, 16);
   e = cudaMalloc((void**)&t->Wh, b_wh);
   if (e == cudaSuccess) e = cudaMalloc((void**)&t->Wl, b_wl);
@@ -267,6 +425,22 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   }
   *t->h_err = 0;
   t->ws_bytes = b_wh + b_wl + b_wlo + b_gs + b_ls + b_sc;
+  if ((flags & JET_FLAG_STORE) && mem_budget > 0 && L >= 3) {
+    t->wstore_tile_stride = (long long)(L - 2) * (t->act_bytes + t->alo_bytes) + (long long)(L - 2) * t->act_bytes;
+    t->wstore_budget = mem_budget;
+    if ((long long)(mem_budget / (size_t)t->wstore_tile_stride) > 0) {
+      t->wg_sms = prop.multiProcessorCount;
+      const int ipl = std::max(1, (2 * t->wg_sms + L - 3) / (L - 2));
+      t->wg_max_items = (L - 2) * ipl;
+      const size_t b_wo = (size_t)t->wg_max_items * w * w * sizeof(double);
+      e = cudaMalloc((void**)&t->wg_out, b_wo);
+      if (e != cudaSuccess) {
+        tc_plan_destroy(t);
+        return tcuda(e, "weight-gradient partials");
+      }
+      t->ws_bytes += b_wo;
+    }
+  }
   const int R = 128 * t->H;
   bool ok = encode(&t->wmap, t->Wh, w, w, std::max(1, L - 2), R, 3) &&
             encode(&t->wlmap, t->Wl, w, p->n_out, 1, 128, 2);
@@ -288,6 +462,8 @@ void tc_plan_destroy(TcPlan* t) {
   cudaFree(t->grad_slices);
   cudaFree(t->loss_slices);
   cudaFree(t->scratch);
+  cudaFree(t->wstore);
+  cudaFree(t->wg_out);
   cudaFree(t->err);
   cudaFreeHost(t->h_err);
   if (t->err_ev) cudaEventDestroy(t->err_ev);
@@ -367,6 +543,35 @@ void fill_tc(const jet_plan_s* p, const TcPlan* t, const void* params, const voi
   I.alo_bytes = t->alo_bytes;
   I.r0w = t->r0w;
   I.r1w = t->r1w;
+  I.slice_shared = t->shared_acc ? 1 : 0;
+  const bool use_store = t->wstore && I.n_tiles <= t->wstore_tiles;
+  I.wstore = use_store ? t->wstore : nullptr;
+  I.wstore_tile_stride = t->wstore_tile_stride;
+}
+
+// Grow the weight-gradient store to the tiles of N points when the plan's
+// budget allows; otherwise the call runs in per-tile mode.  A call that grows
+// it allocates (and cudaFree synchronises): make the first call with the
+// largest N before any stream capture.
+void ensure_store(TcPlan* t, long long N) {
+  if (!t->wstore_budget || !t->wg_out || N < 1) return;
+  const long long tiles = (N + t->P - 1) / t->P;
+  if (tiles <= t->wstore_tiles) return;
+  const size_t need = (size_t)tiles * (size_t)t->wstore_tile_stride;
+  if (need > t->wstore_budget) return;
+  if (t->wstore) {
+    cudaFree(t->wstore);
+    t->ws_bytes -= (size_t)t->wstore_tiles * (size_t)t->wstore_tile_stride;
+    t->wstore = nullptr;
+    t->wstore_tiles = 0;
+  }
+  if (cudaMalloc((void**)&t->wstore, need) == cudaSuccess) {
+    t->wstore_tiles = tiles;
+    t->ws_bytes += need;
+  } else {
+    t->wstore = nullptr;
+    cudaGetLastError();  // clear: this N runs in per-tile mode
+  }
 }
 
 jet_status prep(const jet_plan_s* p, TcPlan* t, const void* params, cudaStream_t s) {
@@ -391,8 +596,53 @@ jet_status run(jet_plan_s* p, TcPlan* t, int mode, const TcInst& I, cudaStream_t
   a.err = t->err;
   a.tmem_cols = t->tmem_cols;
   const int grid = std::min(t->grid, I.n_chunks);
+  if (mode != MODE_FWD && t->shared_acc) {
+    cudaError_t z = cudaMemsetAsync(t->grad_slices, 0, (size_t)p->n_params * sizeof(double), s);
+    if (z != cudaSuccess) return tcuda(z, "accumulator reset");
+  }
   jet::plan_prof_begin(p, s);
   cudaError_t e = tc_launch(p->cls, a, grid, t->smem, s);
+  if (e == cudaSuccess && mode != MODE_FWD && I.wstore) {
+    // weight gradients of the hidden-to-hidden layers from the store
+    WgArgs w;
+    memset(&w, 0, sizeof(w));
+    const int L = p->L, R = 128 * t->H;
+    w.wstore = I.wstore;
+    w.tile_stride = t->wstore_tile_stride;
+    w.a_slot = t->act_bytes + t->alo_bytes;
+    w.z_off = (long long)(L - 2) * w.a_slot;
+    w.act_bytes = t->act_bytes;
+    w.chunk_bytes = (R / 8) * 1024;
+    w.ach = t->act_bytes / w.chunk_bytes;
+    w.stages = std::min(kWgMaxStages, (int)((200 * 1024) / (2 * w.chunk_bytes)));
+    w.L = L;
+    w.w = t->w;
+    w.H = t->H;
+    w.n_tiles = I.n_tiles;
+    w.items_per_layer = t->wg_max_items / (L - 2);
+    w.tiles_per_item = (I.n_tiles + w.items_per_layer - 1) / w.items_per_layer;
+    w.items_per_layer = (int)((I.n_tiles + w.tiles_per_item - 1) / w.tiles_per_item);
+    w.n_items = (L - 2) * w.items_per_layer;
+    w.out = t->wg_out;
+    w.err = t->err;
+    int tm = 32;
+    while (tm < t->H * t->w) tm *= 2;
+    w.tmem_cols = tm;
+    const size_t smem = (size_t)w.stages * 2 * w.chunk_bytes + 1024;
+    e = cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      wgrad_kernel<<<std::min(w.n_items, t->wg_sms), kWgThreads, smem, s>>>(w);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      OffWl ow;
+      for (int l = 0; l < L; ++l) ow.v[l] = p->off_W[l];
+      const long long tot = (long long)(L - 2) * t->w * t->w;
+      wgrad_sum_kernel<<<(int)std::min<long long>((tot + 255) / 256, 2048), 256, 0, s>>>(
+          t->wg_out, L, t->w, w.items_per_layer, ow, t->grad_slices);
+      e = cudaGetLastError();
+    }
+  }
   jet::plan_prof_end(p, s);
   if (e != cudaSuccess) return tcuda(e, "tc kernel launch");
   e = cudaMemcpyAsync(t->h_err, t->err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -438,6 +688,7 @@ jet_status tc_backward(jet_plan_s* p, TcPlan* t, const void* params, const void*
     if (loss_out) cudaMemsetAsync(loss_out, 0, sizeof(double), s);
     return JET_OK;
   }
+  ensure_store(t, N);
   st = prep(p, t, params, s);
   if (st != JET_OK) return st;
   TcInst I;
@@ -450,6 +701,7 @@ jet_status tc_backward(jet_plan_s* p, TcPlan* t, const void* params, const void*
   j.loss_slices = I.loss_slices;
   j.n_chunks = I.n_chunks;
   j.n_params = p->n_params;
+  j.grad_chunks = t->shared_acc ? 1 : 0;
   j.inv_N = I.inv_N;
   j.grad_out = grad_out;
   j.loss_out = loss_out;
@@ -461,6 +713,7 @@ jet_status tc_train_step(jet_plan_s* p, TcPlan* t, void* params, void* m, void* 
                          const void* X, long long N, const void* source, double* loss_out, cudaStream_t s) {
   jet_status st = check_err(t);
   if (st != JET_OK) return st;
+  ensure_store(t, N);
   st = prep(p, t, params, s);
   if (st != JET_OK) return st;
   TcInst I;
@@ -473,6 +726,7 @@ jet_status tc_train_step(jet_plan_s* p, TcPlan* t, void* params, void* m, void* 
   j.loss_slices = I.loss_slices;
   j.n_chunks = I.n_chunks;
   j.n_params = p->n_params;
+  j.grad_chunks = t->shared_acc ? 1 : 0;
   j.inv_N = I.inv_N;
   j.loss_out = loss_out;
   j.params = params;
@@ -606,6 +860,7 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
     I.loss_slices = b->loss_slices + (long long)i * b->max_chunks;
     I.scratch = b->scratch;
     I.scratch_stride = b->scratch_stride;
+    I.slice_shared = 0;  // batches keep one deterministic slice per chunk
     double per_tile = (double)(p->L - 1) * t->w * t->w * t->cols_pad + 2000.0 * t->w * t->P * (p->L - 1);
     for (int c = 0; c < I.n_chunks; ++c) {
       const long long t0 = (long long)c * I.tiles_per_chunk;

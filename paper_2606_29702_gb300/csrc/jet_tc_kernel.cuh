@@ -91,6 +91,12 @@ struct alignas(64) TcInst {
   int o_w, o_wlo, o_a0, o_a1, o_alo0, o_alo1, o_uo, o_ub, o_xs, o_red;
   int act_bytes, alo_bytes;
   int r0w, r1w;  // TMEM column widths of regions R0 and R1 per half
+  int slice_shared;  // 1: all chunks add into grad_slices[0 .. n_params)
+  // store mode: per tile, the layer inputs A^1..A^{L-2} (and their split low
+  // parts) and the adjoints Zbar^2..Zbar^{L-1} go to HBM for the separate
+  // weight-gradient GEMM; null = per-tile weight-gradient MMA and flush
+  unsigned char* wstore;
+  long long wstore_tile_stride;  // bytes per tile
 };
 
 struct TcArgs {
@@ -168,8 +174,19 @@ struct TcTile {
     for (int kc = 0; kc < nck; ++kc) tc::tma_load_2d(sm + I.o_w + kc * box, &I.wlmap, bar_tma, kc * 64, 0);
   }
 
-  __device__ unsigned char* slot(int l) const {  // scratch copy of A^l, l = 1..L-3
-    return I.scratch + (long long)blockIdx.x * I.scratch_stride + (long long)(l - 1) * (I.act_bytes + I.alo_bytes);
+  long long cur_tile = 0;
+
+  // copy of A^l (l = 1..L-3; with the store also L-2): per-CTA scratch slot,
+  // or the tile's place in the store
+  __device__ unsigned char* slot(int l) const {
+    const long long off = (long long)(l - 1) * (I.act_bytes + I.alo_bytes);
+    if (I.wstore) return I.wstore + cur_tile * I.wstore_tile_stride + off;
+    return I.scratch + (long long)blockIdx.x * I.scratch_stride + off;
+  }
+  // adjoint Zbar^l (l = 2..L-1) of the tile in the store
+  __device__ unsigned char* zslot(int l) const {
+    return I.wstore + cur_tile * I.wstore_tile_stride + (long long)(I.L - 2) * (I.act_bytes + I.alo_bytes) +
+           (long long)(l - 2) * I.act_bytes;
   }
 
   // ------------------------------------------------------------ MMAs (thread 0)
@@ -590,6 +607,9 @@ struct TcTile {
     const long long n0 = t * P;
     const long long rem = I.N - n0;
     const int nvalid = rem < (long long)P ? (int)rem : P;
+    cur_tile = t;
+    const bool store = bwd && I.wstore != nullptr;
+    const int last_a = store ? L - 2 : L - 3;  // highest A^l copied out of shared memory
     float* xs = XS();
     for (int i = tid; i < P * d; i += kTcThreads) {
       const int n = i / d;
@@ -605,8 +625,9 @@ struct TcTile {
     layer1_fwd(0);
     tc::fence_proxy_async_smem();
     sync();
-    // scratch keeps A^l for l <= L-3 (A^{L-2} stays in shared memory for the backward)
-    if (tid == 0 && bwd && L >= 4 && !*abort_f) {
+    // scratch keeps A^l for l <= L-3 (A^{L-2} stays in shared memory for the
+    // backward); the store keeps A^{L-2} as well, for the weight-gradient GEMM
+    if (tid == 0 && bwd && 1 <= last_a && !*abort_f) {
       tc::bulk_s2g(slot(1), ACT(0), (uint32_t)I.act_bytes);
       if (I.split3) tc::bulk_s2g(slot(1) + I.act_bytes, ALO(0), (uint32_t)I.alo_bytes);
       tc::bulk_commit();
@@ -629,7 +650,7 @@ struct TcTile {
       hidden_epilogue(l, cur ^ 1);
       tc::fence_proxy_async_smem();
       sync();
-      if (tid == 0 && bwd && l <= L - 3) {
+      if (tid == 0 && bwd && l <= last_a) {
         tc::bulk_s2g(slot(l), ACT(cur ^ 1), (uint32_t)I.act_bytes);
         if (I.split3) tc::bulk_s2g(slot(l) + I.act_bytes, ALO(cur ^ 1), (uint32_t)I.alo_bytes);
         tc::bulk_commit();
@@ -685,6 +706,20 @@ struct TcTile {
       tc::fence_proxy_async_smem();
       sync();
       part_flush(0, g + I.off_b[l - 1], 1);  // bias gradient of layer l
+      if (store) {
+        // Zbar^l goes to the store; the weight gradient is a separate GEMM
+        if (tid == 0) {
+          tc::bulk_s2g(zslot(l), ACT(zb), (uint32_t)I.act_bytes);
+          tc::bulk_commit();
+          mma_dgrad(zb);
+          tc::mma_commit(bar_mma);
+        }
+        if (!wait(bar_mma, ph_mma, 66)) break;
+        tc::tc_fence_after();
+        if (tid == 0) tc::bulk_wait_read0();  // ACT(zb) is rewritten by the next adjoint
+        sync();
+        continue;
+      }
       const int NB = I.H == 2 ? 128 : I.w;
       const int nblk = I.w / NB;
       if (tid == 0) {
@@ -772,8 +807,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
     TcTile<Cls> T{I,   sm,      &bars[0], &bars[1], &bars[2], &abort_s,      args.err, tmem_s, ph_tma,
                   ph_mma, ph_ld, tid,      warp,     128 * I.H, &part_s[0], warp & 3, warp >> 2, tid & 127};
     const bool bwd = args.mode != MODE_FWD;
-    double* g = bwd ? I.grad_slices + (long long)chunk * I.n_params : nullptr;
-    if (bwd)
+    // one FP64 slice per chunk (fixed summation order), or one accumulator
+    // shared by every chunk, zeroed by the host, when the slices would not
+    // fit in L2
+    double* g = bwd ? I.grad_slices + (I.slice_shared ? 0LL : (long long)chunk * I.n_params) : nullptr;
+    if (bwd && !I.slice_shared)
       for (long long i = tid; i < I.n_params; i += kTcThreads) g[i] = 0.0;
     __syncthreads();
     double loss = 0.0;
