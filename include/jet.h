@@ -250,6 +250,16 @@ jet_status jet_backward_params_noalloc(const jet_residual_spec* spec, int32_t d_
                                        const void* source, void* grad_out, double* loss_out,
                                        jet_stream_t stream, size_t* scratch_bytes_used);
 
+/*
+ * Verification hook for failure detection: launches one CTA that waits on an
+ * mbarrier nothing arrives at, with the same bounded wait the tensor-core
+ * kernels use and a budget of budget_ns nanoseconds (1e3..1e9).  The kernel
+ * gives up, records the time-out and returns; the call synchronises and
+ * returns JET_ERR_TIMEOUT (the device context stays usable).  Any other
+ * status means the bounded wait or its reporting is broken.
+ */
+jet_status jet_debug_wait_timeout(int64_t budget_ns);
+
 /* Thread-local message for the last failing call on this thread. */
 const char* jet_last_error(void);
 

@@ -939,3 +939,38 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
   e = launch_reduce(b->d_jobs, b->h_jobs[0], n, maxp, false, adam, step, lr, s);
   return e == cudaSuccess ? JET_OK : tcuda(e, "batch reduce");
 }
+
+// ------------------------------------------------------------------ failure-detection hook
+namespace {
+__global__ void wait_timeout_kernel(unsigned long long budget_ns, int* err) {
+  __shared__ uint64_t bar;
+  __shared__ volatile int abort_s;
+  if (threadIdx.x == 0) {
+    abort_s = 0;
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  // nothing arrives at the barrier: the bounded wait must give up
+  const bool ok = tc::mbar_wait(&bar, 0u, &abort_s, err, 90, budget_ns);
+  if (ok && threadIdx.x == 0) atomicExch(err, -1);  // a wait that "completed" is a failure of the hook
+}
+}  // namespace
+
+extern "C" jet_status jet_debug_wait_timeout(int64_t budget_ns) {
+  if (budget_ns < 1000 || budget_ns > 1000000000) return tfail(JET_ERR_INVALID, "budget_ns must be in [1e3, 1e9]");
+  int* d_err = nullptr;
+  cudaError_t e = cudaMalloc((void**)&d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    wait_timeout_kernel<<<1, 32>>>((unsigned long long)budget_ns, d_err);
+    e = cudaGetLastError();
+  }
+  int h = 0;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d_err);
+  if (e != cudaSuccess) return tcuda(e, "wait-timeout hook");
+  if (h == 90) return tfail(JET_ERR_TIMEOUT, "bounded device wait gave up after its budget (as intended)");
+  return tfail(JET_ERR_CUDA, "bounded wait did not report a time-out");
+}

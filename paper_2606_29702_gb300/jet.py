@@ -53,7 +53,7 @@ class JetPlanInfo(ctypes.Structure):
 EXPORTS = ["jet_plan_create", "jet_plan_get_info", "jet_forward_residual", "jet_backward_params", "jet_train_step",
            "jet_plan_destroy", "jet_batch_create", "jet_batch_backward", "jet_batch_train_step", "jet_batch_destroy",
            "jet_debug_activation", "jet_plan_profile", "jet_plan_profile_read", "jet_backward_params_noalloc",
-           "jet_last_error", "jet_version"]
+           "jet_debug_wait_timeout", "jet_last_error", "jet_version"]
 
 _lib = None
 
@@ -85,6 +85,7 @@ def load():
     L.jet_backward_params_noalloc.argtypes = [ctypes.POINTER(JetResidualSpec), i32, i32, ctypes.POINTER(i32), i32,
                                               ctypes.POINTER(JetChan), i32, vp, vp, i64, vp, vp, vp, vp,
                                               ctypes.POINTER(sz)]
+    L.jet_debug_wait_timeout.argtypes = [i64]
     L.jet_plan_profile.argtypes = [vp, i32]
     L.jet_plan_profile_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
     L.jet_last_error.restype = ctypes.c_char_p
@@ -319,3 +320,9 @@ class JetResidual(torch.autograd.Function):
 def plan_for(name, widths, precision="fp32", **coefs):
     """Convenience: a plan for a named PDE family of ``specs``."""
     return Plan(_specs.by_name(name, **coefs), widths, precision)
+
+
+def debug_wait_timeout(budget_ns=1_000_000):
+    """Status of jet_debug_wait_timeout (JET_ERR_TIMEOUT == 6 when the bounded wait works)."""
+    L = load()
+    return L.jet_debug_wait_timeout(int(budget_ns))
