@@ -81,6 +81,14 @@ typedef enum {
  * kernel cannot run (JET_ERR_UNSUPPORTED); 0 keeps the built-in choice. */
 #define JET_FLAG_TILE(p8) (((p8)&0xff) << 8)
 #define JET_FLAG_TILE_GET(flags) (((flags) >> 8) & 0xff)
+/* CTA shape override of the tensor-core kernel (used by the autotuner):
+ * n = 1 runs one CTA of 16 warps per SM, n = 2 two CTAs of 8 warps per SM
+ * (each with its own tile, so one CTA's activation epilogue overlaps the
+ * other's MMAs and copies).  0 keeps the built-in choice; a shape whose tile
+ * does not fit shared memory or TMEM gives JET_ERR_UNSUPPORTED.  Ignored by
+ * the FP64 and FP32 forms. */
+#define JET_FLAG_CTAS(n) (((n)&0x3) << 16)
+#define JET_FLAG_CTAS_GET(flags) (((flags) >> 16) & 0x3)
 
 /* One derivative channel d^alpha u_out: alpha[i] = order in coordinate i. */
 typedef struct {
@@ -115,6 +123,8 @@ typedef struct {
   int32_t tile_points;     /* points per tile of the fused kernel */
   int32_t grid_ctas;       /* persistent CTAs per launch */
   size_t workspace_bytes;  /* device memory the plan owns */
+  int32_t ctas_per_sm;     /* CTAs of the fused kernel resident per SM */
+  int32_t cta_threads;     /* threads per CTA of the fused kernel */
 } jet_plan_info;
 
 /*

@@ -2,9 +2,10 @@
 
 For a plan shape (residual spec, layer widths, precision) it builds plans with
 each candidate tile size (points per tile, which fixes the MMA N extent of the
-tensor-core kernel and the per-CTA chunking of the work list), times the
-parameter-gradient call with CUDA events on representative points, and keeps
-the fastest.  Results are cached in a JSON file keyed by the shape, so that
+tensor-core kernel and the per-CTA chunking of the work list), weight-gradient
+schedule and CTA shape (one CTA of 16 warps or two of 8 warps per SM), times
+the parameter-gradient call with CUDA events on representative points, and
+keeps the fastest.  Results are cached in a JSON file keyed by the shape, so that
 later plans of the same shape reuse the choice without timing.
 
 The cache path is ``$JET_TUNE_CACHE`` when set, else ``jet_tune_cache.json``
@@ -64,45 +65,52 @@ STORE_BUDGET = 96 << 30
 
 
 def tune(spec, widths, precision, params, X, source=None, candidates=DEFAULT_CANDIDATES, reps=3, path=None,
-         timer=None, schedules=None):
-    """Time every (tile size, weight-gradient schedule) pair; cache and return
-    (best_tile, {tile: ms}) -- the ms of each tile's faster schedule.
+         timer=None, schedules=None, ctas=None):
+    """Time every (tile size, weight-gradient schedule, CTA shape) triple;
+    cache and return (best_tile, {tile: ms}) -- the ms of each tile's fastest
+    schedule and shape.
 
     Schedules of the tensor-core forms: "tile" (weight gradient flushed per
     tile, bounded memory) and "store" (layer inputs and adjoints in HBM, one
-    weight-gradient GEMM per layer); the SIMT forms have one schedule.
+    weight-gradient GEMM per layer); CTA shapes 1 (16 warps) and 2 (two CTAs
+    of 8 warps per SM).  The SIMT forms have one schedule and shape.
     """
     timer = timer or _time_plan
+    tc = precision in ("bf16", "bf16x3", "tf32")
     if schedules is None:
-        schedules = ("tile", "store") if precision in ("bf16", "bf16x3", "tf32") else ("tile",)
-    results, sched = {}, {}
+        schedules = ("tile", "store") if tc else ("tile",)
+    if ctas is None:
+        ctas = (1, 2) if tc else (0,)
+    results, choice = {}, {}
     for P in candidates:
         for sc in schedules:
-            kw = dict(store=True, mem_budget=STORE_BUDGET) if sc == "store" else {}
-            try:
-                plan = jet.Plan(spec, widths, precision, tile=P, **kw)
-            except jet.JetError:
-                continue  # does not fit shared memory / TMEM for this shape
-            try:
-                ms = float(timer(plan, params, X, source, reps))
-            finally:
-                plan.close()
-            if P not in results or ms < results[P]:
-                results[P], sched[P] = ms, sc
+            for nc in ctas:
+                kw = dict(store=True, mem_budget=STORE_BUDGET) if sc == "store" else {}
+                try:
+                    plan = jet.Plan(spec, widths, precision, tile=P, ctas=nc, **kw)
+                except jet.JetError:
+                    continue  # does not fit shared memory / TMEM for this shape
+                try:
+                    ms = float(timer(plan, params, X, source, reps))
+                finally:
+                    plan.close()
+                if P not in results or ms < results[P]:
+                    results[P], choice[P] = ms, (sc, nc)
     if not results:
         raise RuntimeError("no candidate tile size fits this shape")
     best = min(results, key=lambda k: (results[k], k))
     cache = load_cache(path)
-    cache[shape_key(spec, widths, precision)] = {"tile": int(best), "schedule": sched[best],
+    cache[shape_key(spec, widths, precision)] = {"tile": int(best), "schedule": choice[best][0],
+                                                 "ctas": int(choice[best][1]),
                                                  "ms": {str(k): v for k, v in results.items()}}
     save_cache(cache, path)
     return best, results
 
 
 def tuned(spec, widths, precision, path=None):
-    """Cached (tile, schedule) for the shape, or None."""
+    """Cached (tile, schedule, ctas) for the shape, or None."""
     e = load_cache(path).get(shape_key(spec, widths, precision))
-    return None if e is None else (int(e["tile"]), e.get("schedule", "tile"))
+    return None if e is None else (int(e["tile"]), e.get("schedule", "tile"), int(e.get("ctas", 0)))
 
 
 def tuned_tile(spec, widths, precision, path=None):
@@ -119,4 +127,5 @@ def plan(spec, widths, precision, path=None, **kw):
     if t[1] == "store":
         kw.setdefault("store", True)
         kw.setdefault("mem_budget", STORE_BUDGET)
+    kw.setdefault("ctas", t[2])
     return jet.Plan(spec, widths, precision, tile=t[0], **kw)

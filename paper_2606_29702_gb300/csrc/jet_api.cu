@@ -295,7 +295,7 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
   for (int l = 1; l < n_layers; ++l) wmax = std::max(wmax, widths[l]);
   const int p8 = JET_FLAG_TILE_GET(flags);
   p->P = p8 ? 8 * p8 : tile_points(p->C, wmax, p->fp64);
-  p->pitch = pitch_for(p->C * p->P, p->fp64);
+  p->pitch = pitch_for(simt_point_stride(p->C) * p->P, p->fp64);
   p->smem = smem_bytes(p->C, p->P, p->pitch, wmax, n_out, d_in, p->elem);
   cudaDeviceProp prop;
   cudaError_t e = cudaGetDeviceProperties(&prop, p->device);
@@ -311,6 +311,7 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
       return e != cudaSuccess ? cuda_fail(e, "occupancy") : fail(JET_ERR_UNSUPPORTED, "SIMT tile does not fit one SM");
     }
     p->grid = prop.multiProcessorCount * per_sm;
+    p->ctas_per_sm = per_sm;
   }
 
   // ---- workspace
@@ -318,7 +319,7 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
   for (int l = 1; l < n_layers; ++l) jet_elems += (long long)p->C * p->P * widths[l];
   if (!p->tc) {
     p->scratch_stride = jet_elems;
-    size_t b_wt = (size_t)p->n_params * p->elem;
+    size_t b_wt = (size_t)weight_ws_elems(p->n_params) * p->elem;
     size_t b_gs = (size_t)p->grid * p->n_params * sizeof(double);
     size_t b_ls = (size_t)p->grid * sizeof(double);
     size_t b_sc = (size_t)p->grid * jet_elems * p->elem;
@@ -370,6 +371,8 @@ jet_status jet_plan_get_info(jet_plan_t p, jet_plan_info* info) {
   info->tile_points = p->tc ? tc_tile_points(p->tcp) : p->P;
   info->grid_ctas = p->tc ? tc_grid(p->tcp) : p->grid;
   info->workspace_bytes = p->tc ? tc_workspace_bytes(p->tcp) : p->ws_bytes;
+  info->ctas_per_sm = p->tc ? tc_ctas_per_sm(p->tcp) : p->ctas_per_sm;
+  info->cta_threads = p->tc ? tc_threads(p->tcp) : kSimtThreads;
   return JET_OK;
 }
 
@@ -719,7 +722,7 @@ jet_status jet_batch_create(jet_batch_t* out, int32_t n, const jet_plan_t* plans
     b->slice_off.push_back(slices);
     slices += (long long)b->max_chunks_per_inst * plans[i]->n_params;
     b->wt_off.push_back(wt);
-    wt += plans[i]->n_params;
+    wt += weight_ws_elems(plans[i]->n_params);
   }
   b->smem = smem;
   int per_sm = 0, dev = 0;

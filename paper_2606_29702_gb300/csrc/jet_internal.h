@@ -37,7 +37,9 @@ struct DevInstance {
   long long off_b[kMaxLayers];
   long long n_params;
   const void* params;  // packed, value type T
-  const void* Wt;      // packed transposed weights (plan workspace), value type T
+  const void* Wt;      // weight workspace, value type T: the packed parameters
+                       // with every W^l transposed, then (at weight_copy_offset)
+                       // a 16-byte-aligned copy of the packed parameters
   const void* X;       // [N][d]
   const void* source;  // [N][n_res] or null
   void* r_out;         // [N][n_res] or null
@@ -56,7 +58,7 @@ struct DevInstance {
   double* grad_slices;
   double* loss_slices;
   // z-jet store for MODE_FWD / MODE_BWD_STORE: per tile, per hidden layer,
-  // [C * P][w] (unit fastest); null if not stored
+  // [w][C * P] (as the shared-memory rows); null if not stored
   void* store;
   long long store_tile_stride;  // elements per tile
 };
@@ -74,6 +76,12 @@ struct SimtArgs {
 };
 
 constexpr int kSimtThreads = 256;
+// Point stride of a SIMT shared-memory jet row [unit][n * S + alpha]: odd, so
+// that lanes walking points n hit distinct banks.
+__host__ __device__ constexpr int simt_point_stride(int C) { return C | 1; }
+// elements of the SIMT weight workspace: transposed copy, then aligned copy
+__host__ __device__ inline long long weight_copy_offset(long long n_params) { return (n_params + 3) & ~3LL; }
+__host__ __device__ inline long long weight_ws_elems(long long n_params) { return 2 * weight_copy_offset(n_params); }
 // Dynamic shared memory of the fused SIMT kernel: three jet buffers
 // [wmax][pitch], output jets and adjoints [n_out*C][P], tile points [P][d],
 // and a small reduction area.

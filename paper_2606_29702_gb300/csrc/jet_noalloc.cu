@@ -198,7 +198,7 @@ extern "C" jet_status jet_backward_params_noalloc(const jet_residual_spec* spec,
   // tiling: same rule as the plan path
   const int TP = fp64 ? 2 : 4;
   const int P = TP * (kSimtThreads / wmax > 0 ? kSimtThreads / wmax : 1);
-  int pitch = C * P;
+  int pitch = simt_point_stride(C) * P;
   while (pitch % (fp64 ? 16 : 32) != (fp64 ? 2 : 4)) ++pitch;
   I.P = P;
   I.pitch = pitch;
@@ -209,7 +209,7 @@ extern "C" jet_status jet_backward_params_noalloc(const jet_residual_spec* spec,
 
   // carve the static array: Wt | loss slices | grad slices | per-CTA scratch
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t b_wt = up((size_t)I.n_params * elem);
+  const size_t b_wt = up((size_t)weight_ws_elems(I.n_params) * elem);
   const size_t per_chunk = (size_t)I.n_params * sizeof(double) + sizeof(double) + (size_t)jet_elems * elem;
   const size_t fixed = b_wt + 3 * 256;
   if (fixed + per_chunk > kStaticScratchBytes)

@@ -27,7 +27,7 @@ struct jet_plan_s {
   std::vector<long long> off_W, off_b;
   int P = 0, pitch = 0;
   size_t smem = 0;
-  int grid = 0;
+  int grid = 0, ctas_per_sm = 0;
   size_t elem = 4;
   // workspace
   void* Wt = nullptr;

@@ -1,4 +1,4 @@
-// Weight transposition, deterministic FP64 gradient/loss reduction over the
+// Weight transposition (plus an aligned copy of the parameters), deterministic FP64 gradient/loss reduction over the
 // chunk slices, and the fused full-batch Adam update (Sec. 3.1.1).
 #include "jet_internal.h"
 
@@ -7,8 +7,10 @@ namespace jet {
 template <class T>
 __global__ void transpose_weights_kernel(const __grid_constant__ DevInstance I, T* Wt) {
   const T* P = reinterpret_cast<const T*>(I.params);
+  T* Wc = Wt + weight_copy_offset(I.n_params);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < I.n_params;
        e += (long long)gridDim.x * blockDim.x) {
+    Wc[e] = P[e];
     for (int l = 0; l < I.L; ++l) {
       const long long off = I.off_W[l];
       const int fi = I.widths[l], fo = I.widths[l + 1];

@@ -15,14 +15,18 @@
 //             composition), weight gradient sum_cols Zb A^T, bias gradient on
 //             the value channel, data gradient W^T Zb.
 //
-// Jets live in shared memory as [unit][channel-major column] rows:
-// column = alpha * P + n.  A thread owns one unit and TP consecutive points of
-// every channel, so the composition and its adjoint are thread-local.  The
-// hidden z-jets of a tile are written to a per-CTA global scratch slot (or to
-// a full-size store) in the forward and read back in the backward: the
-// memory of the backward is bounded by the number of CTAs, not by N.
-// Gradient partial sums go to a per-(instance, chunk) FP64 slice that exactly
-// one CTA updates, so the final FP64 reduction is deterministic.
+// Jets live in shared memory as [unit][point-major column] rows: column =
+// n * S + alpha with an odd point stride S >= C (the pad columns stay zero).
+// A thread owns one point and TP consecutive units with every channel, so the
+// composition and its adjoint are thread-local and each jet-GEMM activation
+// load is one conflict-free wavefront.  The hidden z-jets of a tile are
+// written to a per-CTA global scratch slot (or to a full-size store) as
+// [unit][alpha * P + n] in the forward and read back in the backward, cached
+// in L2 only so that L1 keeps the layer's weights: the memory of the backward
+// is bounded by the number of CTAs, not by N.
+// Gradient partial sums go to a per-(instance, chunk) FP64 slice; every slice
+// element is added by one thread in tile order (fire-and-forget FP64 adds),
+// so the final FP64 reduction is deterministic.
 #pragma once
 
 #include "jet_closures_gen.h"
@@ -61,6 +65,16 @@ __device__ __forceinline__ void vload(const T* p, T* out) {
   for (int j = 0; j < Vec<T>::N; ++j) out[j] = q[j];
 }
 
+// Vec<T>::N consecutive values through the read-only path (16-byte aligned)
+template <class T>
+__device__ __forceinline__ void vldg(const T* p, T* out) {
+  using V = typename Vec<T>::type;
+  V v = __ldg(reinterpret_cast<const V*>(p));
+  const T* q = reinterpret_cast<const T*>(&v);
+#pragma unroll
+  for (int j = 0; j < Vec<T>::N; ++j) out[j] = q[j];
+}
+
 template <class T>
 __device__ __forceinline__ void vstore(T* p, const T* in) {
   using V = typename Vec<T>::type;
@@ -82,6 +96,8 @@ struct SimtTile {
   static constexpr int NP = Cls::NP;
   static constexpr int TP = Vec<T>::N;
   static constexpr int NT = kSimtThreads;
+  static constexpr int RU = TP;  // consecutive units per thread
+  static constexpr int S = simt_point_stride(C);  // row stride of one point
 
   const DevInstance& I;
   const SimtArgs& A;
@@ -90,14 +106,15 @@ struct SimtTile {
   T* UB;     // output adjoints [n_out*C][P]
   T* XS;     // tile points [P][d]
   double* RED;
-  int P, pitch;
+  int P, pitch, wmax;
   const T* params;
-  const T* Wt;
+  const T* Wt;  // transposed weights [in][out] per layer
+  const T* Wc;  // aligned copy of the packed parameters
 
   __device__ SimtTile(const DevInstance& I_, const SimtArgs& A_, unsigned char* smem) : I(I_), A(A_) {
     P = I.P;
     pitch = I.pitch;
-    int wmax = 0;
+    wmax = 0;
     for (int l = 1; l < I.L; ++l) wmax = max(wmax, I.widths[l]);
     T* base = reinterpret_cast<T*>(smem);
     size_t be = (size_t)wmax * pitch;
@@ -112,6 +129,7 @@ struct SimtTile {
     RED = reinterpret_cast<double*>(smem + off);
     params = reinterpret_cast<const T*>(I.params);
     Wt = reinterpret_cast<const T*>(I.Wt);
+    Wc = Wt + weight_copy_offset(I.n_params);
   }
 
   __device__ const T* W(int l) const { return params + I.off_W[l - 1]; }   // l = 1..L
@@ -127,24 +145,34 @@ struct SimtTile {
   }
 
   // ---------------------------------------------------------------- forward
+  // Every elementwise phase and both jet GEMMs map a thread to one point n of
+  // the tile and RU consecutive units u0 .. u0+RU, with all C channels of each
+  // (unit, point) in registers: lanes walk points, so a point's channels sit
+  // at fixed offsets from one row pointer, shared-memory rows (odd stride S)
+  // are read and written conflict-free, the z-jet scratch rows
+  // [unit][alpha * P + n] are coalesced, and with RU = TP every thread has
+  // exactly one item when the tile fills the CTA (P = TP * threads / width).
   __device__ void layer1(T* out, T* zdst) {
-    const int w = I.widths[1], d = I.d;
+    const int w = I.widths[1], d = I.d, CP = C * P;
     const T* W1 = W(1);
     const T* b1 = bias(1);
-    const int ngrp = P / TP;
-    for (int it = threadIdx.x; it < w * ngrp; it += NT) {
-      const int u = it % w, pg = it / w;
-      T wrow[3];
-      for (int i = 0; i < 3; ++i) wrow[i] = i < d ? W1[u * d + i] : T(0);
-      const T bu = b1[u];
+    for (int it = threadIdx.x; it < (w / RU) * P; it += NT) {
+      const int n = it % P, u0 = (it / P) * RU;
+      T x[3];
 #pragma unroll
-      for (int j = 0; j < TP; ++j) {
-        const int n = pg * TP + j;
+      for (int i = 0; i < 3; ++i) x[i] = i < d ? XS[n * d + i] : T(0);
+#pragma unroll
+      for (int r = 0; r < RU; ++r) {
+        const int u = u0 + r;
+        T wrow[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) wrow[i] = i < d ? W1[u * d + i] : T(0);
         T z[C], p[NP], a[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) z[c] = T(0);
-        T v = bu;
-        for (int i = 0; i < d; ++i) v += wrow[i] * XS[n * d + i];
+        T v = b1[u];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) v += wrow[i] * x[i];
         z[0] = v;
 #pragma unroll
         for (int i = 0; i < Cls::D; ++i) {
@@ -154,87 +182,80 @@ struct SimtTile {
         tanh_derivs<T, NP>(z[0], p);
         Cls::compose(z, p, a);
 #pragma unroll
-        for (int c = 0; c < C; ++c) out[u * pitch + c * P + n] = a[c];
+        for (int c = 0; c < C; ++c) out[u * pitch + n * S + c] = a[c];
         if (zdst) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) zdst[(long long)(c * P + n) * w + u] = z[c];
+          for (int c = 0; c < C; ++c) __stcg(zdst + (long long)u * CP + c * P + n, z[c]);
         }
       }
     }
   }
 
-  // Z^l = W^l A^{l-1} (+ b on channel 0), then a^l = compose(z^l).
+  // Z^l = W^l A^{l-1} (+ b on channel 0), then a^l = compose(z^l).  Per k a
+  // thread reads its point's C activations (one shared-memory wavefront per
+  // load: lanes walk points) and RU weights as one vector, for RU * C FMAs.
   __device__ void hidden_fwd(int l, const T* in, T* out, T* zdst) {
-    const int wi = I.widths[l - 1], wo = I.widths[l];
+    const int wi = I.widths[l - 1], wo = I.widths[l], CP = C * P;
     const T* Wtl = WtL(l);  // [wi][wo]
     const T* bl = bias(l);
-    const int ngrp = P / TP;
-    for (int it = threadIdx.x; it < wo * ngrp; it += NT) {
-      const int u = it % wo, pg = it / wo;
-      T acc[C][TP];
+    for (int it = threadIdx.x; it < (wo / RU) * P; it += NT) {
+      const int n = it % P, u0 = (it / P) * RU;
+      T acc[RU][C];
 #pragma unroll
-      for (int c = 0; c < C; ++c)
+      for (int r = 0; r < RU; ++r)
 #pragma unroll
-        for (int j = 0; j < TP; ++j) acc[c][j] = T(0);
-      const T* inp = in + pg * TP;
+        for (int c = 0; c < C; ++c) acc[r][c] = T(0);
+      const T* ap = in + n * S;  // row k of A^{l-1}, this point's channels
+      const T* wp = Wtl + u0;    // row k of W^l^T, this thread's units
 #pragma unroll 2
-      for (int k = 0; k < wi; ++k) {
-        const T wv = __ldg(Wtl + k * wo + u);
+      for (int k = 0; k < wi; ++k, ap += pitch, wp += wo) {
+        T wv[RU], av[C];
+        vldg<T>(wp, wv);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          T v[TP];
-          vload<T>(inp + k * pitch + c * P, v);
+        for (int c = 0; c < C; ++c) av[c] = ap[c];
 #pragma unroll
-          for (int j = 0; j < TP; ++j) acc[c][j] = fma(wv, v[j], acc[c][j]);
-        }
+        for (int r = 0; r < RU; ++r)
+#pragma unroll
+          for (int c = 0; c < C; ++c) acc[r][c] = fma(wv[r], av[c], acc[r][c]);
       }
-      const T bu = bl[u];
-      T outv[C][TP];
 #pragma unroll
-      for (int j = 0; j < TP; ++j) {
+      for (int r = 0; r < RU; ++r) {
+        const int u = u0 + r;
         T z[C], p[NP], a[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) z[c] = acc[c][j];
-        z[0] += bu;
+        for (int c = 0; c < C; ++c) z[c] = acc[r][c];
+        z[0] += bl[u];
         tanh_derivs<T, NP>(z[0], p);
         Cls::compose(z, p, a);
 #pragma unroll
-        for (int c = 0; c < C; ++c) outv[c][j] = a[c];
+        for (int c = 0; c < C; ++c) out[u * pitch + n * S + c] = a[c];
         if (zdst) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) zdst[(long long)(c * P + pg * TP + j) * wo + u] = z[c];
+          for (int c = 0; c < C; ++c) __stcg(zdst + (long long)u * CP + c * P + n, z[c]);
         }
       }
-#pragma unroll
-      for (int c = 0; c < C; ++c) vstore<T>(out + u * pitch + c * P + pg * TP, outv[c]);
     }
   }
 
-  // a^l = compose(z^l) from a stored z-jet [C*P][w]
+  // a^l = compose(z^l) from a stored z-jet [w][C*P]
   __device__ void compose_from(int l, const T* zsrc, T* out) {
-    const int w = I.widths[l];
-    const int ngrp = P / TP;
-    for (int it = threadIdx.x; it < w * ngrp; it += NT) {
-      const int u = it % w, pg = it / w;
-      // all loads of the point group first, so that they are in flight together
-      T zz[C][TP];
+    const int w = I.widths[l], CP = C * P;
+    for (int it = threadIdx.x; it < (w / RU) * P; it += NT) {
+      const int n = it % P, u0 = (it / P) * RU;
+      // all loads first, so that they are in flight together
+      T zz[RU][C];
 #pragma unroll
-      for (int c = 0; c < C; ++c)
+      for (int r = 0; r < RU; ++r)
 #pragma unroll
-        for (int j = 0; j < TP; ++j) zz[c][j] = zsrc[(long long)(c * P + pg * TP + j) * w + u];
-      T outv[C][TP];
+        for (int c = 0; c < C; ++c) zz[r][c] = __ldcg(zsrc + (long long)(u0 + r) * CP + c * P + n);
 #pragma unroll
-      for (int j = 0; j < TP; ++j) {
-        T z[C], p[NP], a[C];
+      for (int r = 0; r < RU; ++r) {
+        T p[NP], a[C];
+        tanh_derivs<T, NP>(zz[r][0], p);
+        Cls::compose(zz[r], p, a);
 #pragma unroll
-        for (int c = 0; c < C; ++c) z[c] = zz[c][j];
-        tanh_derivs<T, NP>(z[0], p);
-        Cls::compose(z, p, a);
-#pragma unroll
-        for (int c = 0; c < C; ++c) outv[c][j] = a[c];
+        for (int c = 0; c < C; ++c) out[(u0 + r) * pitch + n * S + c] = a[c];
       }
-#pragma unroll
-      for (int c = 0; c < C; ++c) vstore<T>(out + u * pitch + c * P + pg * TP, outv[c]);
     }
   }
 
@@ -245,9 +266,10 @@ struct SimtTile {
     const T* bL = bias(L);
     const int ncol = C * P;
     for (int it = threadIdx.x; it < no * ncol; it += NT) {
-      const int o = it / ncol, col = it % ncol;
+      const int o = it / ncol, col = it % ncol;  // col = alpha * P + n
+      const T* ap = in + (col % P) * S + col / P;
       T s = col < P ? bL[o] : T(0);
-      for (int k = 0; k < wi; ++k) s = fma(WL[o * wi + k], in[k * pitch + col], s);
+      for (int k = 0; k < wi; ++k) s = fma(WL[o * wi + k], ap[k * pitch], s);
       UO[o * ncol + col] = s;
     }
   }
@@ -298,60 +320,55 @@ struct SimtTile {
     const T* WL = W(L);
     const int ncol = C * P;
     for (int it = threadIdx.x; it < wi * ncol; it += NT) {
-      const int k = it / ncol, col = it % ncol;
+      const int k = it / ncol, col = it % ncol;  // col = alpha * P + n
       T s = T(0);
       for (int o = 0; o < no; ++o) s = fma(WL[o * wi + k], UB[o * ncol + col], s);
-      abar[k * pitch + col] = s;
+      abar[k * pitch + (col % P) * S + col / P] = s;
     }
     for (int it = threadIdx.x; it < no * wi; it += NT) {
       const int o = it / wi, k = it % wi;
       T s = T(0);
-      for (int col = 0; col < ncol; ++col) s = fma(UB[o * ncol + col], a_last[k * pitch + col], s);
-      g[I.off_W[L - 1] + o * wi + k] += (double)s;
+      for (int n = 0; n < P; ++n)
+#pragma unroll
+        for (int c = 0; c < C; ++c) s = fma(UB[o * ncol + c * P + n], a_last[k * pitch + n * S + c], s);
+      atomicAdd(g + I.off_W[L - 1] + o * wi + k, (double)s);
     }
     for (int o = threadIdx.x; o < no; o += NT) {
       T s = T(0);
       for (int n = 0; n < P; ++n) s += UB[o * ncol + n];
-      g[I.off_b[L - 1] + o] += (double)s;
+      atomicAdd(g + I.off_b[L - 1] + o, (double)s);
     }
   }
 
   // Zbar^l = (d compose / dz)^T Abar^l, per (unit, point), z^l read from zsrc.
   __device__ void act_adjoint(int l, const T* zsrc, const T* abar, T* zbar) {
-    const int w = I.widths[l];
-    const int ngrp = P / TP;
-    for (int it = threadIdx.x; it < w * ngrp; it += NT) {
-      const int u = it % w, pg = it / w;
-      T abv[C][TP], outv[C][TP], zz[C][TP];
-      // all global loads of the point group first, so that they overlap
+    const int w = I.widths[l], CP = C * P;
+    for (int it = threadIdx.x; it < (w / RU) * P; it += NT) {
+      const int n = it % P, u0 = (it / P) * RU;
+      // all global loads first, so that they overlap
+      T zz[RU][C];
 #pragma unroll
-      for (int c = 0; c < C; ++c)
+      for (int r = 0; r < RU; ++r)
 #pragma unroll
-        for (int j = 0; j < TP; ++j) zz[c][j] = zsrc[(long long)(c * P + pg * TP + j) * w + u];
+        for (int c = 0; c < C; ++c) zz[r][c] = __ldcg(zsrc + (long long)(u0 + r) * CP + c * P + n);
 #pragma unroll
-      for (int c = 0; c < C; ++c) vload<T>(abar + u * pitch + c * P + pg * TP, abv[c]);
+      for (int r = 0; r < RU; ++r) {
+        const int u = u0 + r;
+        T p[NP], ab[C], zb[C];
 #pragma unroll
-      for (int j = 0; j < TP; ++j) {
-        T z[C], p[NP], ab[C], zb[C];
+        for (int c = 0; c < C; ++c) ab[c] = abar[u * pitch + n * S + c];
+        tanh_derivs<T, NP>(zz[r][0], p);
+        Cls::adjoint(zz[r], p, ab, zb);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          z[c] = zz[c][j];
-          ab[c] = abv[c][j];
-        }
-        tanh_derivs<T, NP>(z[0], p);
-        Cls::adjoint(z, p, ab, zb);
-#pragma unroll
-        for (int c = 0; c < C; ++c) outv[c][j] = zb[c];
+        for (int c = 0; c < C; ++c) zbar[u * pitch + n * S + c] = zb[c];
       }
-#pragma unroll
-      for (int c = 0; c < C; ++c) vstore<T>(zbar + u * pitch + c * P + pg * TP, outv[c]);
     }
   }
 
   // dW^l[u][k] += sum_cols Zbar[u][col] A[k][col]; db^l[u] += sum_n Zbar[u][n]
   __device__ void wgrad(int l, const T* zbar, const T* aprev, double* g) {
     const int wo = I.widths[l], wi = I.widths[l - 1];
-    const int ncol = C * P;
+    const int ncol = S * P;  // every column, the zero pads of odd S included
     const int nkb = wi / 4;
     double* gW = g + I.off_W[l - 1];
     for (int it = threadIdx.x; it < (wo / 4) * nkb; it += NT) {
@@ -374,50 +391,51 @@ struct SimtTile {
 #pragma unroll
             for (int j = 0; j < TP; ++j) acc[r][s] = fma(zv[r][j], av[s][j], acc[r][s]);
       }
+      // fire-and-forget FP64 adds: every slice element belongs to one thread,
+      // which adds the tiles in order, so the sums stay deterministic
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int s = 0; s < 4; ++s) gW[(ub * 4 + r) * wi + kb + s * nkb] += (double)acc[r][s];
+        for (int s = 0; s < 4; ++s) atomicAdd(gW + (ub * 4 + r) * wi + kb + s * nkb, (double)acc[r][s]);
     }
     double* gb = g + I.off_b[l - 1];
     for (int u = threadIdx.x; u < wo; u += NT) {
       T s = T(0);
-      for (int n = 0; n < P; n += TP) {
-        T v[TP];
-        vload<T>(zbar + u * pitch + n, v);
-#pragma unroll
-        for (int j = 0; j < TP; ++j) s += v[j];
-      }
-      gb[u] += (double)s;
+      for (int n = 0; n < P; ++n) s += zbar[u * pitch + n * S];
+      atomicAdd(gb + u, (double)s);
     }
   }
 
-  // Abar^{l-1}[k][col] = sum_u W^l[u][k] Zbar^l[u][col]
+  // Abar^{l-1}[k][col] = sum_u W^l[u][k] Zbar^l[u][col].  A thread owns one
+  // point and RU consecutive input units (the mapping of hidden_fwd); the
+  // weights W^l[u][k0 .. k0+RU) come from the aligned parameter copy.
   __device__ void dgrad(int l, const T* zbar, T* abar) {
     const int wo = I.widths[l], wi = I.widths[l - 1];
-    const T* Wl = W(l);  // [wo][wi]
-    const int ngrp = P / TP;
-    for (int it = threadIdx.x; it < wi * ngrp; it += NT) {
-      const int k = it % wi, pg = it / wi;
-      T acc[C][TP];
+    const T* Wl = Wc + I.off_W[l - 1];  // [wo][wi]
+    for (int it = threadIdx.x; it < (wi / RU) * P; it += NT) {
+      const int n = it % P, k0 = (it / P) * RU;
+      T acc[RU][C];
 #pragma unroll
-      for (int c = 0; c < C; ++c)
+      for (int i = 0; i < RU; ++i)
 #pragma unroll
-        for (int j = 0; j < TP; ++j) acc[c][j] = T(0);
-      const T* zp = zbar + pg * TP;
+        for (int c = 0; c < C; ++c) acc[i][c] = T(0);
+      const T* zp = zbar + n * S;  // row u of Zbar^l, this point's channels
+      const T* wp = Wl + k0;       // row u of W^l, this thread's input units
 #pragma unroll 2
-      for (int u = 0; u < wo; ++u) {
-        const T wv = __ldg(Wl + u * wi + k);
+      for (int u = 0; u < wo; ++u, zp += pitch, wp += wi) {
+        T wv[RU], zv[C];
+        vldg<T>(wp, wv);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          T v[TP];
-          vload<T>(zp + u * pitch + c * P, v);
+        for (int c = 0; c < C; ++c) zv[c] = zp[c];
 #pragma unroll
-          for (int j = 0; j < TP; ++j) acc[c][j] = fma(wv, v[j], acc[c][j]);
-        }
+        for (int i = 0; i < RU; ++i)
+#pragma unroll
+          for (int c = 0; c < C; ++c) acc[i][c] = fma(wv[i], zv[c], acc[i][c]);
       }
 #pragma unroll
-      for (int c = 0; c < C; ++c) vstore<T>(abar + k * pitch + c * P + pg * TP, acc[c]);
+      for (int i = 0; i < RU; ++i)
+#pragma unroll
+        for (int c = 0; c < C; ++c) abar[(k0 + i) * pitch + n * S + c] = acc[i][c];
     }
   }
 
@@ -429,18 +447,22 @@ struct SimtTile {
     for (int u = threadIdx.x; u < w; u += NT) {
       T sb = T(0), sw[3] = {T(0), T(0), T(0)};
       for (int n = 0; n < P; ++n) {
-        const T z0 = zbar[u * pitch + n];
+        const T z0 = zbar[u * pitch + n * S];
         sb += z0;
-        for (int i = 0; i < d; ++i) sw[i] = fma(z0, XS[n * d + i], sw[i]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          if (i < d) sw[i] = fma(z0, XS[n * d + i], sw[i]);
       }
 #pragma unroll
       for (int i = 0; i < Cls::D; ++i) {
         const int fo = Cls::first_order(i);
         if (fo >= 0 && i < d)
-          for (int n = 0; n < P; ++n) sw[i] += zbar[u * pitch + fo * P + n];
+          for (int n = 0; n < P; ++n) sw[i] += zbar[u * pitch + n * S + fo];
       }
-      for (int i = 0; i < d; ++i) gW[u * d + i] += (double)sw[i];
-      gb[u] += (double)sb;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i < d) atomicAdd(gW + u * d + i, (double)sw[i]);
+      atomicAdd(gb + u, (double)sb);
     }
   }
 
@@ -508,6 +530,10 @@ __global__ void __launch_bounds__(kSimtThreads) simt_kernel(const __grid_constan
     const DevInstance& I = args.insts ? args.insts[args.item_inst[args.n_items + item]] : args.inst0;
     const int chunk = item - I.chunk_base;
     SimtTile<Cls, T> S(I, args, smem);
+    // the pad columns of the odd point stride are never written: zero them
+    // (and everything else) once per item so that the weight-gradient sums
+    // over whole rows see zeros there
+    for (int i = threadIdx.x; i < 3 * S.wmax * S.pitch; i += kSimtThreads) S.B[0][i] = T(0);
     const bool bwd = args.mode != MODE_FWD;
     double* g = bwd ? I.grad_slices + (long long)chunk * I.n_params : nullptr;
     if (bwd)

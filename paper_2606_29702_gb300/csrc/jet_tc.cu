@@ -21,13 +21,15 @@ using namespace jet;
 namespace jet {
 
 template <int ID> cudaError_t tc_launch_id(const TcArgs& a, int grid, size_t smem, cudaStream_t s);
-template <int ID> cudaError_t tc_max_active_id(size_t smem, int* blocks);
+template <int ID> cudaError_t tc_max_active_id(size_t smem, int threads, int* blocks);
+template <int ID> cudaError_t tc_attrs_id(cudaFuncAttributes* a);
 
 struct TcPlan {
   int w = 0, H = 1, P = 0, cols = 0, cols_pad = 0, top_cols = 0, split3 = 0;
   int tmem_cols = 0, ctas_per_sm = 1, grid = 0;
+  int nthreads = 512;  // CTA size: 512 (one CTA per SM) or 256 (two)
   size_t smem = 0;
-  int o_w, o_wlo, o_a0, o_a1, o_alo0, o_alo1, o_uo, o_ub, o_xs, o_red;
+  int o_w, o_wlo, o_a0, o_a1, o_alo0, o_alo1, o_uo, o_ub, o_xs, o_red, o_part;
   int act_bytes = 0, alo_bytes = 0, r0w = 0, r1w = 0;
   long long scratch_stride = 0;
   // workspace
@@ -56,7 +58,7 @@ struct TcPlan {
 };
 
 // budget of the per-chunk gradient slices (they are updated once per tile)
-constexpr double kSliceBudgetBytes = 32.0 * 1024 * 1024;
+constexpr double kSliceBudgetBytes = 48.0 * 1024 * 1024;
 
 // ------------------------------------------------------------------ weight-gradient GEMM
 // Wbar^l = sum over the tiles of a K range of Zbar^l A^{l-1}^T, both operands
@@ -216,15 +218,48 @@ cudaError_t tc_launch(int cls, const TcArgs& a, int grid, size_t smem, cudaStrea
   return cudaErrorInvalidValue;
 }
 
-cudaError_t tc_occupancy(int cls, size_t smem, int* blocks) {
+cudaError_t tc_occupancy(int cls, size_t smem, int threads, int* blocks) {
   switch (cls) {
 #define CASE(id, cl) \
   case id:           \
-    return tc_max_active_id<id>(smem, blocks);
+    return tc_max_active_id<id>(smem, threads, blocks);
     JET_FOR_EACH_CLASS(CASE)
 #undef CASE
   }
   return cudaErrorInvalidValue;
+}
+
+// CTAs of the fused kernel that fit one SM by registers and shared memory.
+// The runtime's occupancy query reports one CTA per SM for any kernel that
+// contains TMEM instructions; measured residency shows two such CTAs running
+// on one SM at once when their TMEM allocations fit together (the plan keeps
+// the sum at or below 512 columns), so the count is derived here from the
+// kernel's own attributes.
+cudaError_t tc_fit(int cls, size_t smem, int threads, int* blocks) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (cls) {
+#define CASE(id, cl)            \
+  case id:                      \
+    e = tc_attrs_id<id>(&a);    \
+    break;
+    JET_FOR_EACH_CLASS(CASE)
+#undef CASE
+  }
+  if (e != cudaSuccess) return e;
+  int dev = 0, smem_sm = 0, regs_sm = 0, reserved = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e != cudaSuccess) return e;
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = (a.numRegs * 32 + 255) / 256 * 256;  // 256-register allocation unit
+  const size_t smem_cta = smem + a.sharedSizeBytes + (size_t)reserved;
+  const int by_regs = regs_sm / std::max(1, warps * regs_warp);
+  const int by_smem = (int)((size_t)smem_sm / std::max<size_t>(1, smem_cta));
+  *blocks = std::min(by_regs, by_smem);
+  return cudaSuccess;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -320,6 +355,8 @@ size_t carve(TcPlan& t, int C, int n_out, int d) {
   off = (off + 15) / 16 * 16;
   t.o_red = (int)off;
   off += 64;
+  t.o_part = (int)off;
+  off += (size_t)(t.nthreads / 128) * 4 * 256 * sizeof(float);
   return off;
 }
 
@@ -352,42 +389,69 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   t->H = w > 128 ? 2 : 1;
   t->split3 = p->prec == JET_BF16X3 ? 1 : 0;
   const int ntop = C - top_begin;
-  // choose P: most points per SM (P x CTAs per SM), shared memory <= 220 KB,
-  // TMEM <= 512 columns per SM
+  // choose the CTA shape and P: most points in flight per SM (P x CTAs per
+  // SM) within shared memory and TMEM (512 columns per SM); on a tie two CTAs
+  // of 8 warps, whose epilogues and MMAs overlap, win over one of 16 warps
   int best_score = -1;
   TcPlan best = *t;
-  const int p8 = JET_FLAG_TILE_GET(flags);
-  for (int P = p8 ? 8 * p8 : 8; P <= (p8 ? 8 * p8 : 64); P += 8) {
-    TcPlan c = *t;
-    c.P = P;
-    c.cols = C * P;
-    c.cols_pad = (c.cols + 15) / 16 * 16;
-    if (c.cols_pad > 256) break;
-    c.top_cols = ntop * P;
-    if (c.split3 && c.top_cols % 16) continue;
-    const size_t sm = carve(c, C, p->n_out, p->d) + 1024;
-    if (sm > 208 * 1024) continue;  // + ~17 KB of static shared memory per CTA
-    const int NB = c.H == 2 ? 128 : w;
-    c.r0w = std::max(c.cols_pad, NB);
-    c.r1w = c.cols_pad;
-    const int need = c.H * (c.r0w + c.r1w);
-    int tm = 32;
-    while (tm < need) tm *= 2;
-    if (tm > 512) continue;
-    c.tmem_cols = tm;
-    const int by_tmem = 512 / tm;
-    int by_occ = 0;  // registers and shared memory
-    if (tc_occupancy(p->cls, sm, &by_occ) != cudaSuccess || by_occ < 1) continue;
-    c.ctas_per_sm = std::max(1, std::min(by_tmem, by_occ));
-    const int score = P * c.ctas_per_sm;
-    if (score > best_score) {
-      best_score = score;
-      best = c;
+  const int p8 = JET_FLAG_TILE_GET(flags), want_ctas = JET_FLAG_CTAS_GET(flags);
+  if (want_ctas > 2) {
+    delete t;
+    return tfail(JET_ERR_INVALID, "JET_FLAG_CTAS takes 0, 1 or 2");
+  }
+  char why[160] = "no candidate tile";  // last rejection, for the error message
+  for (int ctas = 1; ctas <= 2; ++ctas) {
+    if (want_ctas && ctas != want_ctas) continue;
+    for (int P = p8 ? 8 * p8 : 8; P <= (p8 ? 8 * p8 : 64); P += 8) {
+      TcPlan c = *t;
+      c.nthreads = 512 / ctas;
+      c.P = P;
+      c.cols = C * P;
+      c.cols_pad = (c.cols + 15) / 16 * 16;
+      if (c.cols_pad > 256) break;
+      c.top_cols = ntop * P;
+      if (c.split3 && c.top_cols % 16) {
+        snprintf(why, sizeof(why), "P=%d: split columns not a multiple of 16", P);
+        continue;
+      }
+      const size_t sm = carve(c, C, p->n_out, p->d) + 1024;
+      if (sm > (size_t)(226 * 1024) / ctas) {
+        snprintf(why, sizeof(why), "P=%d, %d CTA/SM: %zu B of shared memory", P, ctas, sm);
+        continue;
+      }
+      const int NB = c.H == 2 ? 128 : w;
+      c.r0w = std::max(c.cols_pad, NB);
+      c.r1w = c.cols_pad;
+      const int need = c.H * (c.r0w + c.r1w);
+      int tm = 32;
+      while (tm < need) tm *= 2;
+      if (tm > 512 / ctas) {
+        snprintf(why, sizeof(why), "P=%d, %d CTA/SM: %d TMEM columns", P, ctas, tm);
+        continue;
+      }
+      c.tmem_cols = tm;
+      int by_occ = 0;  // registers and shared memory
+      const cudaError_t oe = ctas == 1 ? tc_occupancy(p->cls, sm, c.nthreads, &by_occ)
+                                       : tc_fit(p->cls, sm, c.nthreads, &by_occ);
+      if (oe != cudaSuccess || by_occ < ctas) {
+        snprintf(why, sizeof(why), "P=%d, %d CTA/SM: occupancy %d (%s, %zu B shared)", P, ctas, by_occ,
+                 cudaGetErrorString(oe), sm);
+        cudaGetLastError();
+        continue;
+      }
+      c.ctas_per_sm = ctas;
+      const int score = 2 * P * ctas + (ctas == 2 ? 1 : 0);
+      if (score > best_score) {
+        best_score = score;
+        best = c;
+      }
     }
   }
   if (best_score < 0) {
     delete t;
-    return tfail(JET_ERR_UNSUPPORTED, "no tile size fits shared memory and TMEM");
+    char msg[224];
+    snprintf(msg, sizeof(msg), "no tile size fits shared memory and TMEM (%s)", why);
+    return tfail(JET_ERR_UNSUPPORTED, msg);
   }
   *t = best;
   // pad the shared-memory request so that no more CTAs share an SM than TMEM allows
@@ -395,7 +459,8 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   const size_t floor_sm = (228 * 1024) / (t->ctas_per_sm + 1) + 1024;
   t->smem = std::max(sm, floor_sm);
   int occ = 0;
-  cudaError_t e = tc_occupancy(p->cls, t->smem, &occ);
+  cudaError_t e = t->ctas_per_sm == 1 ? tc_occupancy(p->cls, t->smem, t->nthreads, &occ)
+                                      : tc_fit(p->cls, t->smem, t->nthreads, &occ);
   if (e != cudaSuccess || occ < 1) {
     delete t;
     return e != cudaSuccess ? tcuda(e, "tc occupancy") : tfail(JET_ERR_UNSUPPORTED, "tensor-core tile does not fit");
@@ -472,6 +537,8 @@ void tc_plan_destroy(TcPlan* t) {
 
 int tc_tile_points(const TcPlan* t) { return t ? t->P : 0; }
 int tc_grid(const TcPlan* t) { return t ? t->grid : 0; }
+int tc_ctas_per_sm(const TcPlan* t) { return t ? t->ctas_per_sm : 0; }
+int tc_threads(const TcPlan* t) { return t ? t->nthreads : 0; }
 size_t tc_workspace_bytes(const TcPlan* t) { return t ? t->ws_bytes : 0; }
 
 namespace {
@@ -539,6 +606,7 @@ void fill_tc(const jet_plan_s* p, const TcPlan* t, const void* params, const voi
   I.o_ub = t->o_ub;
   I.o_xs = t->o_xs;
   I.o_red = t->o_red;
+  I.o_part = t->o_part;
   I.act_bytes = t->act_bytes;
   I.alo_bytes = t->alo_bytes;
   I.r0w = t->r0w;
@@ -595,6 +663,7 @@ jet_status run(jet_plan_s* p, TcPlan* t, int mode, const TcInst& I, cudaStream_t
   a.item_inst = nullptr;
   a.err = t->err;
   a.tmem_cols = t->tmem_cols;
+  a.nthreads = t->nthreads;
   const int grid = std::min(t->grid, I.n_chunks);
   if (mode != MODE_FWD && t->shared_acc) {
     cudaError_t z = cudaMemsetAsync(t->grad_slices, 0, (size_t)p->n_params * sizeof(double), s);
@@ -745,6 +814,7 @@ jet_status tc_train_step(jet_plan_s* p, TcPlan* t, void* params, void* m, void* 
 namespace jet {
 struct TcBatch {
   int n = 0, cls = 0, grid = 0, tmem_cols = 0, max_chunks = 16, max_items = 0, n_items = 0;
+  int nthreads = 512;  // smallest CTA of the member plans (their partial-sum areas fit it)
   size_t smem = 0;
   TcInst* d_insts = nullptr;
   TcInst* h_insts = nullptr;
@@ -773,6 +843,7 @@ jet_status tc_batch_create(const std::vector<jet_plan_s*>& plans, TcBatch** out)
     TcPlan* t = p->tcp;
     b->smem = std::max(b->smem, t->smem);
     b->tmem_cols = std::max(b->tmem_cols, t->tmem_cols);
+    b->nthreads = std::min(b->nthreads, t->nthreads);
     b->scratch_stride = std::max(b->scratch_stride, t->scratch_stride);
     b->slice_off.push_back(slices);
     slices += (long long)b->max_chunks * p->n_params;
@@ -780,7 +851,8 @@ jet_status tc_batch_create(const std::vector<jet_plan_s*>& plans, TcBatch** out)
   int dev = 0, sms = 0, occ = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = tc_occupancy(b->cls, b->smem, &occ);
+  if (e == cudaSuccess)
+    e = b->nthreads < 512 ? tc_fit(b->cls, b->smem, b->nthreads, &occ) : tc_occupancy(b->cls, b->smem, b->nthreads, &occ);
   if (e != cudaSuccess || occ < 1) {
     delete b;
     return e != cudaSuccess ? tcuda(e, "batch occupancy") : tfail(JET_ERR_UNSUPPORTED, "batch tile does not fit");
@@ -905,6 +977,7 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
   a.item_inst = b->d_items;
   a.err = b->err;
   a.tmem_cols = b->tmem_cols;
+  a.nthreads = b->nthreads;
   cudaError_t e = tc_launch(b->cls, a, std::min(b->grid, base), b->smem, s);
   if (e != cudaSuccess) return tcuda(e, "batched tc kernel launch");
   long long maxp = 0;

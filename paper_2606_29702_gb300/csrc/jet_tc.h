@@ -19,6 +19,8 @@ jet_status tc_plan_create(jet_plan_s* p, jet::TcPlan** out, const cudaDeviceProp
 void tc_plan_destroy(jet::TcPlan* t);
 int tc_tile_points(const jet::TcPlan* t);
 int tc_grid(const jet::TcPlan* t);
+int tc_ctas_per_sm(const jet::TcPlan* t);
+int tc_threads(const jet::TcPlan* t);
 size_t tc_workspace_bytes(const jet::TcPlan* t);
 jet_status tc_forward(jet_plan_s* p, jet::TcPlan* t, const void* params, const void* X, long long N,
                       const void* source, void* r_out, double* loss_out, cudaStream_t s);

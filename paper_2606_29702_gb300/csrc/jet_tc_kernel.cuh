@@ -41,8 +41,10 @@
 
 namespace jet {
 
-constexpr int kTcThreads = 512;
-constexpr int kTcWG = 4;  // warpgroups; each covers the four TMEM lane quadrants
+// A CTA has 2 or 4 warpgroups (TcArgs::nthreads = 256 or 512); each
+// warpgroup covers the four TMEM lane quadrants and a share of the points.
+constexpr int kTcThreads = 512;  // largest CTA
+constexpr int kTcWG = 4;         // largest warpgroup count
 
 // p[k] = tanh^(k)(z) for the tensor-core epilogue.  q = 1 - tanh|z| =
 // 2 / (exp(2|z|) + 1) is formed with the approximate exp2 and reciprocal
@@ -89,6 +91,7 @@ struct alignas(64) TcInst {
   long long scratch_stride;  // bytes per CTA slot
   // shared-memory carve (bytes from the 1024-aligned base)
   int o_w, o_wlo, o_a0, o_a1, o_alo0, o_alo1, o_uo, o_ub, o_xs, o_red;
+  int o_part;  // per-warpgroup partial sums, float [warpgroups][4][256]
   int act_bytes, alo_bytes;
   int r0w, r1w;  // TMEM column widths of regions R0 and R1 per half
   int slice_shared;  // 1: all chunks add into grad_slices[0 .. n_params)
@@ -107,6 +110,7 @@ struct TcArgs {
   const int* item_inst;
   int* err;
   int tmem_cols;
+  int nthreads;  // launch block size: 256 or 512
 };
 
 template <class Cls>
@@ -128,8 +132,9 @@ struct TcTile {
   uint32_t ph_tma, ph_mma, ph_ld;
   int tid, warp;
   int R;        // rows of every operand buffer (128 * H)
-  float* part;  // per-warpgroup partial sums [kTcWG][4][256]
+  float* part;  // per-warpgroup partial sums [nwg][4][256]
   int q, wg, ul;  // TMEM lane quadrant, warpgroup, unit within a 128-row half
+  int nwg, nthr;  // warpgroups and threads of the CTA
 
   // column block of channel c: highest-order channels first
   static __device__ __forceinline__ int blk(int c) { return c >= TOP ? c - TOP : c + (C - TOP); }
@@ -289,7 +294,7 @@ struct TcTile {
       float w1[3] = {0.f, 0.f, 0.f};
       for (int i = 0; i < I.d; ++i) w1[i] = Pm[I.off_W[0] + u * I.d + i];
       const float b1 = Pm[I.off_b[0] + u];
-      for (int g = wg * PPF; g < I.P; g += kTcWG * PPF) {
+      for (int g = wg * PPF; g < I.P; g += nwg * PPF) {
         float av[C][PPF];
 #pragma unroll
         for (int j = 0; j < PPF; ++j) {
@@ -324,7 +329,7 @@ struct TcTile {
       const int u = h * 128 + ul;
       if (h * 128 + q * 32 >= I.w) continue;  // warp-uniform
       const float bu = I.params[I.off_b[l - 1] + u];
-      for (int g = wg * PPF; g < I.P; g += kTcWG * PPF) {
+      for (int g = wg * PPF; g < I.P; g += nwg * PPF) {
         float zv[C][PPF];
 #pragma unroll
         for (int c = 0; c < C; ++c) tc::tmem_ld<PPF>(R0(h) + lane_base() + (uint32_t)(blk(c) * I.P + g), zv[c]);
@@ -372,9 +377,9 @@ struct TcTile {
     const int P = I.P;
     double loss = 0.0;
     if (bwd)
-      for (int i = tid; i < I.n_out * C * P; i += kTcThreads) ub[i] = 0.f;
+      for (int i = tid; i < I.n_out * C * P; i += nthr) ub[i] = 0.f;
     __syncthreads();
-    for (int n = tid; n < nvalid; n += kTcThreads) {
+    for (int n = tid; n < nvalid; n += nthr) {
       float r[kMaxRes];
       for (int c = 0; c < I.n_res; ++c) r[c] = I.source ? -I.source[(n0 + n) * I.n_res + c] : 0.f;
       for (int m = 0; m < I.n_terms; ++m) {
@@ -415,7 +420,7 @@ struct TcTile {
       const int k = h * 128 + ul;
       if (k >= I.w) continue;
       float acc[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
-      for (int c = wg; c < C; c += kTcWG)
+      for (int c = wg; c < C; c += nwg)
         for (int q8 = 0; q8 < P; q8 += 8) {
           const int col = blk(c) * P + q8;
           const uint4 raw = *reinterpret_cast<const uint4*>(ACT(a_buf) + tc::swz_off(k, col, R));
@@ -437,7 +442,7 @@ struct TcTile {
         if (k >= I.w) continue;
         for (int o = 0; o < I.n_out; ++o) {
           double s = 0.0;
-          for (int w2 = 0; w2 < kTcWG; ++w2) s += (double)PART(w2, o, k);
+          for (int w2 = 0; w2 < nwg; ++w2) s += (double)PART(w2, o, k);
           tc::red_add_f64(g + I.off_W[L - 1] + (long long)o * I.w + k, s);
         }
       }
@@ -455,7 +460,7 @@ struct TcTile {
       const int u = h * 128 + ul;
       if (u >= I.w) continue;
       double s = 0.0;
-      for (int w2 = 0; w2 < kTcWG; ++w2) s += (double)PART(w2, k, u);
+      for (int w2 = 0; w2 < nwg; ++w2) s += (double)PART(w2, k, u);
       tc::red_add_f64(dst + (long long)u * stride, s);
     }
   }
@@ -472,7 +477,7 @@ struct TcTile {
       if (abar_from_ub)
         for (int o = 0; o < I.n_out; ++o) wl[o] = I.params[I.off_W[I.L - 1] + (long long)o * I.w + u];
       float gb = 0.f;
-      for (int q = wg * PPB; q < P; q += kTcWG * PPB) {
+      for (int q = wg * PPB; q < P; q += nwg * PPB) {
         float zv[C][PPB], abv[C][PPB];
 #pragma unroll
         for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R0(h) + lane_base() + (uint32_t)(blk(c) * P + q), zv[c]);
@@ -520,7 +525,7 @@ struct TcTile {
     for (int h = 0; h < I.H; ++h) {
       if (h * 128 + q * 32 >= I.w) continue;
       const int j = h * 128 + ul;
-      for (int k0 = wg * 8; k0 < NB; k0 += kTcWG * 8) {
+      for (int k0 = wg * 8; k0 < NB; k0 += nwg * 8) {
         float v[8];
         tc::tmem_ld8(R0(h) + lane_base() + (uint32_t)k0, v);
         tc::tmem_wait_ld();
@@ -547,7 +552,7 @@ struct TcTile {
       if (abar_from_ub)
         for (int o = 0; o < I.n_out; ++o) wl[o] = Pm[I.off_W[I.L - 1] + (long long)o * I.w + u];
       float gw[3] = {0.f, 0.f, 0.f}, gb = 0.f;
-      for (int q = wg * PPB; q < P; q += kTcWG * PPB) {
+      for (int q = wg * PPB; q < P; q += nwg * PPB) {
         float abv[C][PPB];
         if (!abar_from_ub) {
 #pragma unroll
@@ -611,7 +616,7 @@ struct TcTile {
     const bool store = bwd && I.wstore != nullptr;
     const int last_a = store ? L - 2 : L - 3;  // highest A^l copied out of shared memory
     float* xs = XS();
-    for (int i = tid; i < P * d; i += kTcThreads) {
+    for (int i = tid; i < P * d; i += nthr) {
       const int n = i / d;
       xs[i] = n < nvalid ? I.X[(n0 + n) * d + (i % d)] : 0.f;
     }
@@ -757,9 +762,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
   __shared__ uint32_t tmem_s;
   __shared__ volatile int abort_s;
   __shared__ double red_s[kTcThreads / 32];
-  __shared__ float part_s[kTcWG * 4 * 256];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int nthr = args.nthreads, nwg = nthr / 128;
   if (tid == 0) {
     abort_s = 0;
     tc::mbar_init(&bars[0], 1);
@@ -787,12 +792,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
       const int R = 128 * I.H;
       (void)R;
       uint4 z4 = make_uint4(0, 0, 0, 0);
-      for (int i = tid; i < I.act_bytes / 16; i += kTcThreads) {
+      for (int i = tid; i < I.act_bytes / 16; i += nthr) {
         reinterpret_cast<uint4*>(sm + I.o_a0)[i] = z4;
         reinterpret_cast<uint4*>(sm + I.o_a1)[i] = z4;
       }
       if (I.split3)
-        for (int i = tid; i < I.alo_bytes / 16; i += kTcThreads) {
+        for (int i = tid; i < I.alo_bytes / 16; i += nthr) {
           reinterpret_cast<uint4*>(sm + I.o_alo0)[i] = z4;
           reinterpret_cast<uint4*>(sm + I.o_alo1)[i] = z4;
         }
@@ -804,15 +809,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
       __syncthreads();
       prev_inst = ii;
     }
-    TcTile<Cls> T{I,   sm,      &bars[0], &bars[1], &bars[2], &abort_s,      args.err, tmem_s, ph_tma,
-                  ph_mma, ph_ld, tid,      warp,     128 * I.H, &part_s[0], warp & 3, warp >> 2, tid & 127};
+    TcTile<Cls> T{I,
+                  sm,
+                  &bars[0],
+                  &bars[1],
+                  &bars[2],
+                  &abort_s,
+                  args.err,
+                  tmem_s,
+                  ph_tma,
+                  ph_mma,
+                  ph_ld,
+                  tid,
+                  warp,
+                  128 * I.H,
+                  reinterpret_cast<float*>(sm + I.o_part),
+                  warp & 3,
+                  warp >> 2,
+                  tid & 127,
+                  nwg,
+                  nthr};
     const bool bwd = args.mode != MODE_FWD;
     // one FP64 slice per chunk (fixed summation order), or one accumulator
     // shared by every chunk, zeroed by the host, when the slices would not
     // fit in L2
     double* g = bwd ? I.grad_slices + (I.slice_shared ? 0LL : (long long)chunk * I.n_params) : nullptr;
     if (bwd && !I.slice_shared)
-      for (long long i = tid; i < I.n_params; i += kTcThreads) g[i] = 0.0;
+      for (long long i = tid; i < I.n_params; i += nthr) g[i] = 0.0;
     __syncthreads();
     double loss = 0.0;
     const long long t0 = (long long)chunk * I.tiles_per_chunk;
@@ -826,7 +849,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
     __syncthreads();
     if (tid == 0) {
       double s = 0.0;
-      for (int w = 0; w < kTcThreads / 32; ++w) s += red_s[w];
+      for (int w = 0; w < nthr / 32; ++w) s += red_s[w];
       I.loss_slices[chunk] = s;
     }
     __syncthreads();

@@ -47,7 +47,8 @@ class JetPlanInfo(ctypes.Structure):
                 ("n_channels", ctypes.c_int32), ("closure_class", ctypes.c_int32),
                 ("class_name", ctypes.c_char * 32), ("n_params", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("store_mode", ctypes.c_int32), ("store_max_points", ctypes.c_int64),
-                ("tile_points", ctypes.c_int32), ("grid_ctas", ctypes.c_int32), ("workspace_bytes", ctypes.c_size_t)]
+                ("tile_points", ctypes.c_int32), ("grid_ctas", ctypes.c_int32), ("workspace_bytes", ctypes.c_size_t),
+                ("ctas_per_sm", ctypes.c_int32), ("cta_threads", ctypes.c_int32)]
 
 
 EXPORTS = ["jet_plan_create", "jet_plan_get_info", "jet_forward_residual", "jet_backward_params", "jet_train_step",
@@ -135,9 +136,10 @@ class Plan:
     """A libjet plan: one residual on one network shape at one precision."""
 
     def __init__(self, spec, widths, precision="fp32", needed=None, mem_budget=0, store=False, auto_close=True,
-                 tile=None):
+                 tile=None, ctas=0):
         L = load()
         self.tile = tile
+        self.ctas = ctas
         self.spec = spec
         self.widths = list(widths)
         self.precision = precision
@@ -153,6 +155,9 @@ class Plan:
             if tile % 8 or not 8 <= tile <= 2040:
                 raise ValueError("tile must be a multiple of 8 in [8, 2040]")
             flags |= (tile // 8) << 8
+        if ctas not in (0, 1, 2):
+            raise ValueError("ctas must be 0 (plan's choice), 1 or 2")
+        flags |= ctas << 16
         h = ctypes.c_void_p()
         _check(L.jet_plan_create(ctypes.byref(h), ctypes.byref(s), spec.d_in, len(widths) - 1, w, len(needed), nd,
                                  PRECISIONS[precision], int(mem_budget), flags))

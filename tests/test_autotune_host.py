@@ -43,3 +43,38 @@ def test_shape_key_distinguishes_shapes():
     b = autotune.shape_key(specs.allen_cahn(), [2, 32, 1], "bf16")
     c = autotune.shape_key(specs.burgers(0.01), [2, 32, 1], "bf16x3")
     assert len({a, b, c}) == 3
+
+
+class FakeShapedPlan:
+    made = []
+
+    def __init__(self, spec, widths, precision, tile=None, ctas=0, store=False, **kw):
+        if ctas == 2 and tile > 16:
+            raise jet.JetError(3, "two CTAs do not fit")
+        self.key = (tile, ctas, store)
+        FakeShapedPlan.made.append(self.key)
+
+    def close(self):
+        pass
+
+
+def test_tune_picks_cta_shape_and_schedule(tmp_path, monkeypatch):
+    monkeypatch.setattr(jet, "Plan", FakeShapedPlan)
+    path = str(tmp_path / "cache.json")
+    sp = specs.ks()
+    # (tile, ctas, store) -> ms; the two-CTA tile-16 store form is fastest
+    times = {(8, 1, False): 5.0, (8, 1, True): 4.0, (8, 2, False): 3.0, (8, 2, True): 2.5,
+             (16, 1, False): 2.2, (16, 1, True): 2.4, (16, 2, False): 2.0, (16, 2, True): 1.1,
+             (24, 1, False): 1.5, (24, 1, True): 1.6}
+    best, res = autotune.tune(sp, [2, 64, 64, 1], "bf16", None, None, path=path, candidates=(8, 16, 24),
+                              timer=lambda plan, p, x, s, reps: times[plan.key])
+    assert best == 16 and res == {8: 2.5, 16: 1.1, 24: 1.5}
+    assert autotune.tuned(sp, [2, 64, 64, 1], "bf16", path) == (16, "store", 2)
+    FakeShapedPlan.made.clear()
+    autotune.plan(sp, [2, 64, 64, 1], "bf16", path=path)
+    assert FakeShapedPlan.made == [(16, 2, True)]
+    # the SIMT forms are timed with the plan's own shape only
+    FakeShapedPlan.made.clear()
+    autotune.tune(sp, [2, 64, 64, 1], "fp32", None, None, path=path, candidates=(8,),
+                  timer=lambda plan, p, x, s, reps: 1.0)
+    assert FakeShapedPlan.made == [(8, 0, False)]

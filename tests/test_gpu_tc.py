@@ -175,3 +175,46 @@ def test_tc_store_mode_weight_gradient(name, fam, coefs, widths, domain, N, prec
     stored.train_step(p.clone(), m, v, 1, 1e-3, x, s)
     torch.cuda.synchronize()
     assert torch.isfinite(m).all() and float(m.abs().max()) > 0
+
+
+@pytest.mark.parametrize("name,fam,coefs,widths,domain,N,prec,tile", [
+    ("ks_w64", "ks", dict(c1=1.0, c2=1.0, c4=1.0), [2] + [64] * 5 + [1], [(0, 2 * math.pi), (0, 1)], 700, "bf16", 16),
+    ("ns_psi_w128", "ns_psi", dict(nu=0.01), [3] + [128] * 4 + [2], [(0, 1)] * 3, 150, "bf16", 8),
+    ("burgers_w32", "burgers", dict(nu=0.01 / math.pi), [2, 32, 32, 32, 1], DOM2, 333, "bf16", 16),
+    ("allen_cahn_L2", "allen_cahn", dict(eps=1e-4, k=5.0), [2, 128, 1], DOM2, 41, "bf16", 8),
+], ids=["ks", "ns", "burgers", "ac_L2"])
+def test_tc_two_ctas_per_sm(name, fam, coefs, widths, domain, N, prec, tile):
+    """Two CTAs of 8 warps per SM compute what one CTA of 16 warps computes:
+    identical residuals (same tile, same per-point arithmetic), gradients equal
+    up to the order of the FP32 partial sums over warpgroups, both within the
+    oracle bound."""
+    from paper_2606_29702_gb300 import jet
+    sp, X, layers, src, L, r_ref, g_ref = _setup(fam, coefs, widths, domain, N)
+    p = _dev(wl.pack(layers))
+    x = _dev(X)
+    s = None if src is None else _dev(src)
+    one = jet.Plan(sp, widths, prec, tile=tile, ctas=1)
+    two = jet.Plan(sp, widths, prec, tile=tile, ctas=2)
+    i1, i2 = one.info(), two.info()
+    assert (i1["ctas_per_sm"], i1["cta_threads"]) == (1, 512)
+    assert (i2["ctas_per_sm"], i2["cta_threads"]) == (2, 256)
+    r1, l1 = one.forward(p, x, s)
+    r2, l2 = two.forward(p, x, s)
+    g1, _, _ = one.backward(p, x, s)
+    g2, _, _ = two.backward(p, x, s)
+    torch.cuda.synchronize()
+    assert torch.equal(r1, r2)
+    assert abs(float(l1) - float(l2)) <= 1e-12 * abs(float(l1))
+    assert rel_l2(g2.cpu().numpy(), g1.cpu().numpy()) < 1e-5
+    assert rel_l2(r2.cpu().numpy(), r_ref) < TOL[prec][0]
+    assert rel_l2(g2.cpu().numpy(), g_ref) < TOL[prec][1]
+
+
+def test_tc_two_ctas_rejects_wide_layers():
+    """A 256-wide layer's weights alone (128 KB of BF16) exceed half of the
+    SM's shared memory: the two-CTA shape is refused, the default still runs."""
+    from paper_2606_29702_gb300 import jet, specs
+    sp = specs.helmholtz(4 * math.pi)
+    with pytest.raises(jet.JetError):
+        jet.Plan(sp, [3, 256, 256, 1], "bf16", ctas=2)
+    assert jet.Plan(sp, [3, 256, 256, 1], "bf16").info()["ctas_per_sm"] == 1
