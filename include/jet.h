@@ -239,7 +239,7 @@ jet_status jet_plan_profile_read(jet_plan_t plan, int64_t* launches, double* tot
  * or loops that forbid allocator calls after start-up -- and therefore cannot
  * create a plan.  It takes the jet_plan_create arguments (JET_FP64 or
  * JET_FP32 only) together with the jet_backward_params arguments, and keeps
- * all working memory (transposed weights, per-chunk FP64 gradient slices,
+ * all working memory (weight copies, per-chunk FP64 gradient slices,
  * per-CTA jet scratch) in one file-scope device array of 8 MiB that every
  * GPU loading the library reserves until the process exits.
  *   params, X, source, grad_out, loss_out: as jet_backward_params (device;

@@ -69,7 +69,7 @@ def test_noalloc_matches_plan_path_twice(name, prec, N, tol):
 def test_noalloc_rejects_oversized_shape():
     from paper_2606_29702_gb300 import jet, specs
     sp = specs.helmholtz()
-    widths = [3] + [256] * 15 + [1]  # FP64: transposed weights + one gradient slice = 15 MB
+    widths = [3] + [256] * 15 + [1]  # FP64: two weight copies + one gradient slice, about 22 MB
     lib = jet.load()
     s, keep = jet._spec_struct(sp)
     needed = sp.closure()
