@@ -18,7 +18,7 @@ import tempfile
 
 from . import jet
 
-DEFAULT_CANDIDATES = (8, 16, 24, 32, 40, 48, 56, 64)
+DEFAULT_CANDIDATES = (8, 16, 24, 32, 40, 48, 56, 64, 80, 96, 112, 128, 160, 192, 256)
 
 
 def cache_path():

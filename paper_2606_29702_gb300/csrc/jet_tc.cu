@@ -26,6 +26,9 @@ template <int ID> cudaError_t tc_attrs_id(cudaFuncAttributes* a);
 
 struct TcPlan {
   int w = 0, H = 1, P = 0, cols = 0, cols_pad = 0, top_cols = 0, split3 = 0;
+  // packing: G = 128 / wu sub-tiles of Pc points each share the MMA rows
+  // (block-diagonal weights); w = G * wu is the width the MMAs see
+  int wu = 0, G = 1, Pc = 0;
   int tmem_cols = 0, ctas_per_sm = 1, grid = 0;
   int nthreads = 512;  // CTA size: 512 (one CTA per SM) or 256 (two)
   size_t smem = 0;
@@ -186,19 +189,23 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_kernel(const __grid_const
   if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
 }
 
-// dst[off_W[l-1] + r] += sum over the items of layer l of out[item][r]
+// dst[off_W[l-1] + i*wu + k] += sum over the items of layer l and over the
+// G diagonal blocks of out[item] (w = G * wu: packed sub-tiles contribute
+// only within their own block)
 struct OffWl {
   long long v[kMaxLayers];
 };
 
-__global__ void wgrad_sum_kernel(const double* out, int L, int w, int ipl, OffWl offW, double* dst) {
-  const long long ww = (long long)w * w, total = (long long)(L - 2) * ww;
+__global__ void wgrad_sum_kernel(const double* out, int L, int w, int wu, int G, int ipl, OffWl offW, double* dst) {
+  const long long ww = (long long)w * w, uu = (long long)wu * wu, total = (long long)(L - 2) * uu;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const int li = (int)(e / ww);
-    const long long r = e % ww;
+    const int li = (int)(e / uu);
+    const long long r = e % uu;
+    const int i = (int)(r / wu), k = (int)(r % wu);
     double s = 0.0;
-    for (int k = 0; k < ipl; ++k) s += out[((long long)li * ipl + k) * ww + r];
+    for (int it = 0; it < ipl; ++it)
+      for (int b = 0; b < G; ++b) s += out[((long long)li * ipl + it) * ww + (long long)(b * wu + i) * w + b * wu + k];
     dst[offW.v[li + 1] + r] += s;
   }
 }
@@ -296,19 +303,26 @@ struct OffW {
   long long v[kMaxLayers];
 };
 
-__global__ void tc_prep_kernel_v(const float* params, int L, int w, int n_out, OffW offW, __nv_bfloat16* Wh,
+// BF16 copies of the weights in the MMA's view: W^l (l = 2..L-1) as a
+// [w][w] block-diagonal matrix of G copies of the wu x wu weights, and the
+// output weights as [G * n_out][w], row s * n_out + o holding W^L[o] in the
+// columns of sub-tile s (G = 1: plain copies)
+__global__ void tc_prep_kernel_v(const float* params, int L, int w, int wu, int n_out, OffW offW, __nv_bfloat16* Wh,
                                  __nv_bfloat16* Wl, __nv_bfloat16* Wlo, long long nh, long long nl) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nh + nl;
        i += (long long)gridDim.x * blockDim.x) {
     if (i < nh) {
       const long long l = i / ((long long)w * w), r = i % ((long long)w * w);
-      const float v = params[offW.v[l + 1] + r];
+      const int row = (int)(r / w), col = (int)(r % w);
+      const float v = row / wu == col / wu ? params[offW.v[l + 1] + (long long)(row % wu) * wu + col % wu] : 0.f;
       const __nv_bfloat16 hi = __float2bfloat16_rn(v);
       Wh[i] = hi;
       if (Wlo) Wlo[i] = __float2bfloat16_rn(v - __bfloat162float(hi));
     } else {
       const long long r = i - nh;
-      Wl[r] = __float2bfloat16_rn(params[offW.v[L - 1] + r]);
+      const int row = (int)(r / w), col = (int)(r % w);
+      const int sub = row / n_out, o = row % n_out;
+      Wl[r] = __float2bfloat16_rn(col / wu == sub ? params[offW.v[L - 1] + (long long)o * wu + col % wu] : 0.f);
     }
   }
 }
@@ -385,8 +399,12 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
     }
   }
   TcPlan* t = new TcPlan();
-  t->w = w;
-  t->H = w > 128 ? 2 : 1;
+  // widths 32 and 64 pack 4 or 2 sub-tiles into the 128 MMA rows, so that
+  // every TMEM lane quadrant (and so every epilogue warp) holds units
+  t->wu = w;
+  t->G = w <= 64 ? 128 / w : 1;
+  t->w = t->G * w;
+  t->H = t->w > 128 ? 2 : 1;
   t->split3 = p->prec == JET_BF16X3 ? 1 : 0;
   const int ntop = C - top_begin;
   // choose the CTA shape and P: most points in flight per SM (P x CTAs per
@@ -402,14 +420,20 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   char why[160] = "no candidate tile";  // last rejection, for the error message
   for (int ctas = 1; ctas <= 2; ++ctas) {
     if (want_ctas && ctas != want_ctas) continue;
-    for (int P = p8 ? 8 * p8 : 8; P <= (p8 ? 8 * p8 : 64); P += 8) {
+    for (int Pc = 8; Pc <= 64; Pc += 8) {
+      const int P = t->G * Pc;  // points per tile; Pc per sub-tile
+      if (p8 && P != 8 * p8) {
+        if (8 * p8 % (8 * t->G)) snprintf(why, sizeof(why), "P=%d is not a multiple of %d (packed sub-tiles)", 8 * p8, 8 * t->G);
+        continue;
+      }
       TcPlan c = *t;
       c.nthreads = 512 / ctas;
       c.P = P;
-      c.cols = C * P;
+      c.Pc = Pc;
+      c.cols = C * Pc;
       c.cols_pad = (c.cols + 15) / 16 * 16;
       if (c.cols_pad > 256) break;
-      c.top_cols = ntop * P;
+      c.top_cols = ntop * Pc;
       if (c.split3 && c.top_cols % 16) {
         snprintf(why, sizeof(why), "P=%d: split columns not a multiple of 16", P);
         continue;
@@ -419,7 +443,7 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
         snprintf(why, sizeof(why), "P=%d, %d CTA/SM: %zu B of shared memory", P, ctas, sm);
         continue;
       }
-      const int NB = c.H == 2 ? 128 : w;
+      const int NB = c.H == 2 ? 128 : c.w;  // N of the weight-gradient MMA (the MMA width)
       c.r0w = std::max(c.cols_pad, NB);
       c.r1w = c.cols_pad;
       const int need = c.H * (c.r0w + c.r1w);
@@ -469,7 +493,7 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   t->grid = prop.multiProcessorCount * t->ctas_per_sm;
   t->scratch_stride = (long long)std::max(0, L - 3) * (t->act_bytes + t->alo_bytes);
   // workspace
-  const long long nh = (long long)std::max(0, L - 2) * w * w, nl = (long long)p->n_out * w;
+  const long long nh = (long long)std::max(0, L - 2) * t->w * t->w, nl = (long long)t->G * p->n_out * t->w;
   size_t b_wh = std::max<long long>(nh, 1) * 2, b_wl = nl * 2, b_wlo = t->split3 ? b_wh : 0;
   t->shared_acc = (double)t->grid * p->n_params * 8.0 > kSliceBudgetBytes;
   size_t b_gs = (size_t)(t->shared_acc ? 1 : t->grid) * p->n_params * 8, b_ls = (size_t)t->grid * 8;
@@ -497,7 +521,7 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
       t->wg_sms = prop.multiProcessorCount;
       const int ipl = std::max(1, (2 * t->wg_sms + L - 3) / (L - 2));
       t->wg_max_items = (L - 2) * ipl;
-      const size_t b_wo = (size_t)t->wg_max_items * w * w * sizeof(double);
+      const size_t b_wo = (size_t)t->wg_max_items * t->w * t->w * sizeof(double);
       e = cudaMalloc((void**)&t->wg_out, b_wo);
       if (e != cudaSuccess) {
         tc_plan_destroy(t);
@@ -507,9 +531,10 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
     }
   }
   const int R = 128 * t->H;
-  bool ok = encode(&t->wmap, t->Wh, w, w, std::max(1, L - 2), R, 3) &&
-            encode(&t->wlmap, t->Wl, w, p->n_out, 1, 128, 2);
-  if (ok && t->split3) ok = encode(&t->wlomap, t->Wlo, w, w, std::max(1, L - 2), R, 3);
+  const int we = t->w;
+  bool ok = encode(&t->wmap, t->Wh, we, we, std::max(1, L - 2), R, 3) &&
+            encode(&t->wlmap, t->Wl, we, (cuuint64_t)t->G * p->n_out, 1, 128, 2);
+  if (ok && t->split3) ok = encode(&t->wlomap, t->Wlo, we, we, std::max(1, L - 2), R, 3);
   if (!ok) {
     tc_plan_destroy(t);
     return tfail(JET_ERR_UNSUPPORTED, "tensor map encoding failed");
@@ -567,6 +592,9 @@ void fill_tc(const jet_plan_s* p, const TcPlan* t, const void* params, const voi
   I.n_out = p->n_out;
   I.n_res = p->n_res;
   I.w = t->w;
+  I.wu = t->wu;
+  I.G = t->G;
+  I.Pc = t->Pc;
   I.H = t->H;
   I.P = t->P;
   I.cols = t->cols;
@@ -645,10 +673,10 @@ void ensure_store(TcPlan* t, long long N) {
 jet_status prep(const jet_plan_s* p, TcPlan* t, const void* params, cudaStream_t s) {
   OffW ow;
   for (int l = 0; l < p->L; ++l) ow.v[l] = p->off_W[l];
-  const long long nh = (long long)std::max(0, p->L - 2) * t->w * t->w, nl = (long long)p->n_out * t->w;
+  const long long nh = (long long)std::max(0, p->L - 2) * t->w * t->w, nl = (long long)t->G * p->n_out * t->w;
   int grid = (int)std::min<long long>((nh + nl + 255) / 256, 1024);
-  tc_prep_kernel_v<<<grid, 256, 0, s>>>(reinterpret_cast<const float*>(params), p->L, t->w, p->n_out, ow, t->Wh,
-                                        t->Wl, t->Wlo, nh, nl);
+  tc_prep_kernel_v<<<grid, 256, 0, s>>>(reinterpret_cast<const float*>(params), p->L, t->w, t->wu, p->n_out, ow,
+                                        t->Wh, t->Wl, t->Wlo, nh, nl);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? JET_OK : tcuda(e, "tc prep launch");
 }
@@ -706,9 +734,9 @@ jet_status run(jet_plan_s* p, TcPlan* t, int mode, const TcInst& I, cudaStream_t
     if (e == cudaSuccess) {
       OffWl ow;
       for (int l = 0; l < L; ++l) ow.v[l] = p->off_W[l];
-      const long long tot = (long long)(L - 2) * t->w * t->w;
+      const long long tot = (long long)(L - 2) * t->wu * t->wu;
       wgrad_sum_kernel<<<(int)std::min<long long>((tot + 255) / 256, 2048), 256, 0, s>>>(
-          t->wg_out, L, t->w, w.items_per_layer, ow, t->grad_slices);
+          t->wg_out, L, t->w, t->wu, t->G, w.items_per_layer, ow, t->grad_slices);
       e = cudaGetLastError();
     }
   }

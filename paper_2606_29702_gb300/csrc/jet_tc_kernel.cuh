@@ -1,6 +1,10 @@
 // Fused tensor-core partial-jet kernel (BF16 operands, FP32 accumulation in
 // TMEM), one persistent launch over (instance, chunk of point tiles) items.
 //
+// Hidden widths 32 and 64 are packed: G = 128 / width sub-tiles of the tile's
+// points share the 128 MMA rows (operand row = sub-tile * width + unit) with
+// block-diagonal BF16 weights, so that every TMEM lane quadrant holds units.
+//
 // Per tile of P collocation points the CTA keeps the jets of one layer in
 // shared memory as a [unit][column] bf16 matrix in the 128-byte-swizzled
 // layout of tc_ptx.cuh, columns = (channel block, point): the channels of the
@@ -73,6 +77,9 @@ struct alignas(64) TcInst {
   CUtensorMap wlmap;   // output weights bf16 [n_out][w]: dims (in, out), box (64, 128)
   CUtensorMap wlomap;  // low parts of the hidden weights (JET_BF16X3), like wmap
   int L, d, n_out, n_res, w, H, P, cols, cols_pad, top_cols, split3;
+  // packing: operand row r holds unit r % wu of sub-tile r / wu; G = w / wu
+  // sub-tiles of Pc points each (P = G * Pc); w is the width the MMAs see
+  int wu, G, Pc;
   int n_terms;
   DevTerm terms[kMaxTerms];
   const float* params;
@@ -288,13 +295,16 @@ struct TcTile {
   // ------------------------------------------------------------ forward pieces
   __device__ void layer1_fwd(int out_buf) {
     const float* Pm = I.params;
+    const int Pc = I.Pc, d = I.d;
     for (int h = 0; h < I.H; ++h) {
-      const int u = h * 128 + ul;
-      if (u >= I.w) continue;
+      const int r = h * 128 + ul;  // operand row
+      if (r >= I.w) continue;
+      const int sub = r / I.wu, u = r - sub * I.wu;
       float w1[3] = {0.f, 0.f, 0.f};
-      for (int i = 0; i < I.d; ++i) w1[i] = Pm[I.off_W[0] + u * I.d + i];
+      for (int i = 0; i < d; ++i) w1[i] = Pm[I.off_W[0] + u * d + i];
       const float b1 = Pm[I.off_b[0] + u];
-      for (int g = wg * PPF; g < I.P; g += nwg * PPF) {
+      const float* xs = XS() + sub * Pc * d;
+      for (int g = wg * PPF; g < Pc; g += nwg * PPF) {
         float av[C][PPF];
 #pragma unroll
         for (int j = 0; j < PPF; ++j) {
@@ -302,7 +312,7 @@ struct TcTile {
 #pragma unroll
           for (int c = 0; c < C; ++c) z[c] = 0.f;
           float v = b1;
-          for (int i = 0; i < I.d; ++i) v = fmaf(w1[i], XS()[(g + j) * I.d + i], v);
+          for (int i = 0; i < d; ++i) v = fmaf(w1[i], xs[(g + j) * d + i], v);
           z[0] = v;
 #pragma unroll
           for (int i = 0; i < Cls::D; ++i) {
@@ -316,8 +326,8 @@ struct TcTile {
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          st_bf16<PPF>(ACT(out_buf), u, blk(c) * I.P + g, av[c]);
-          if (I.split3 && c >= TOP) st_lo<PPF>(ALO(out_buf), u, blk(c) * I.P + g, av[c]);
+          st_bf16<PPF>(ACT(out_buf), r, blk(c) * Pc + g, av[c]);
+          if (I.split3 && c >= TOP) st_lo<PPF>(ALO(out_buf), r, blk(c) * Pc + g, av[c]);
         }
       }
     }
@@ -325,14 +335,15 @@ struct TcTile {
 
   // a^l = compose(D[R0] + b^l) -> ACT(out_buf)
   __device__ void hidden_epilogue(int l, int out_buf) {
+    const int Pc = I.Pc;
     for (int h = 0; h < I.H; ++h) {
-      const int u = h * 128 + ul;
+      const int r = h * 128 + ul;
       if (h * 128 + q * 32 >= I.w) continue;  // warp-uniform
-      const float bu = I.params[I.off_b[l - 1] + u];
-      for (int g = wg * PPF; g < I.P; g += nwg * PPF) {
+      const float bu = I.params[I.off_b[l - 1] + r % I.wu];
+      for (int g = wg * PPF; g < Pc; g += nwg * PPF) {
         float zv[C][PPF];
 #pragma unroll
-        for (int c = 0; c < C; ++c) tc::tmem_ld<PPF>(R0(h) + lane_base() + (uint32_t)(blk(c) * I.P + g), zv[c]);
+        for (int c = 0; c < C; ++c) tc::tmem_ld<PPF>(R0(h) + lane_base() + (uint32_t)(blk(c) * Pc + g), zv[c]);
         tc::tmem_wait_ld();
         float av[C][PPF];
 #pragma unroll
@@ -348,27 +359,32 @@ struct TcTile {
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          st_bf16<PPF>(ACT(out_buf), u, blk(c) * I.P + g, av[c]);
-          if (I.split3 && c >= TOP) st_lo<PPF>(ALO(out_buf), u, blk(c) * I.P + g, av[c]);
+          st_bf16<PPF>(ACT(out_buf), r, blk(c) * Pc + g, av[c]);
+          if (I.split3 && c >= TOP) st_lo<PPF>(ALO(out_buf), r, blk(c) * Pc + g, av[c]);
         }
       }
     }
   }
 
-  __device__ void out_epilogue() {  // warp 0: UO[o*C + c][n] = D[R1(0)] (+ b^L on the value channel)
-    if (warp != 0) return;
+  // UO[o*C + c][s*Pc + n] = D[R1(0)][row s*n_out + o] (+ b^L on the value
+  // channel).  The rows sit in TMEM lanes 0..G*n_out-1, which the warps of
+  // lane quadrant 0 (one per warpgroup) read, splitting the column groups.
+  __device__ void out_epilogue() {
+    if (q != 0) return;
     float* uo = UO();
-    for (int c = 0; c < C; ++c)
-      for (int g = 0; g < I.P; g += 8) {
-        float v[8];
-        tc::tmem_ld8(R1(0) + (uint32_t)(blk(c) * I.P + g), v);
-        tc::tmem_wait_ld();
-        if (tid < I.n_out) {
-          const float b = c == 0 ? I.params[I.off_b[I.L - 1] + tid] : 0.f;
+    const int Pc = I.Pc, ng = Pc / 8, nrow = I.G * I.n_out;
+    for (int k = wg; k < C * ng; k += nwg) {
+      const int c = k / ng, g = (k - c * ng) * 8;
+      float v[8];
+      tc::tmem_ld8(R1(0) + (uint32_t)(blk(c) * Pc + g), v);
+      tc::tmem_wait_ld();
+      if (ul < nrow) {
+        const int sub = ul / I.n_out, o = ul - sub * I.n_out;
+        const float b = c == 0 ? I.params[I.off_b[I.L - 1] + o] : 0.f;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) uo[(tid * C + c) * I.P + g + j] = v[j] + b;
-        }
+        for (int j = 0; j < 8; ++j) uo[(o * C + c) * I.P + sub * Pc + g + j] = v[j] + b;
       }
+    }
   }
 
   __device__ double residual(long long n0, int nvalid, bool bwd) {
@@ -411,26 +427,37 @@ struct TcTile {
 
   // ------------------------------------------------------------ backward pieces
   // dW^L[o][k] += sum_cols ub[o][col] a^{L-1}[k][col]; db^L[o] += sum_n ub[o][0][n]
-  // (warpgroups split the channel blocks; partials go to PART and are summed
-  // in a fixed order by out_grads_flush after a barrier)
+  // (warpgroups split the channel blocks; partials go to PART per operand
+  // row and are summed in a fixed order, over warpgroups and sub-tiles, by
+  // out_grads_flush after a barrier)
   __device__ void out_grads(int a_buf) {
     const float* ub = UB();
-    const int P = I.P;
+    const int P = I.P, Pc = I.Pc;
     for (int h = 0; h < I.H; ++h) {
-      const int k = h * 128 + ul;
-      if (k >= I.w) continue;
+      const int r = h * 128 + ul;
+      if (r >= I.w) continue;
+      const int sub = r / I.wu;
       float acc[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
       for (int c = wg; c < C; c += nwg)
-        for (int q8 = 0; q8 < P; q8 += 8) {
-          const int col = blk(c) * P + q8;
-          const uint4 raw = *reinterpret_cast<const uint4*>(ACT(a_buf) + tc::swz_off(k, col, R));
+        for (int q8 = 0; q8 < Pc; q8 += 8) {
+          const int col = blk(c) * Pc + q8;
+          const uint4 raw = *reinterpret_cast<const uint4*>(ACT(a_buf) + tc::swz_off(r, col, R));
           const __nv_bfloat16* bv = reinterpret_cast<const __nv_bfloat16*>(&raw);
+          const float* ubc = ub + c * P + sub * Pc + q8;
           for (int o = 0; o < I.n_out; ++o)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[o] = fmaf(__bfloat162float(bv[j]), ub[(o * C + c) * P + q8 + j], acc[o]);
+            for (int j = 0; j < 8; ++j) acc[o] = fmaf(__bfloat162float(bv[j]), ubc[o * C * P + j], acc[o]);
         }
-      for (int o = 0; o < I.n_out; ++o) PART(wg, o, k) = acc[o];
+      for (int o = 0; o < I.n_out; ++o) PART(wg, o, r) = acc[o];
     }
+  }
+
+  // sum of slot k of PART over warpgroups and sub-tiles for true unit u
+  __device__ double part_sum(int k, int u) const {
+    double s = 0.0;
+    for (int sub = 0; sub < I.G; ++sub)
+      for (int w2 = 0; w2 < nwg; ++w2) s += (double)PART(w2, k, sub * I.wu + u);
+    return s;
   }
 
   __device__ void out_grads_flush(double* g) {
@@ -439,12 +466,8 @@ struct TcTile {
     if (wg == 0)
       for (int h = 0; h < I.H; ++h) {
         const int k = h * 128 + ul;
-        if (k >= I.w) continue;
-        for (int o = 0; o < I.n_out; ++o) {
-          double s = 0.0;
-          for (int w2 = 0; w2 < nwg; ++w2) s += (double)PART(w2, o, k);
-          tc::red_add_f64(g + I.off_W[L - 1] + (long long)o * I.w + k, s);
-        }
+        if (k >= I.wu) continue;
+        for (int o = 0; o < I.n_out; ++o) tc::red_add_f64(g + I.off_W[L - 1] + (long long)o * I.wu + k, part_sum(o, k));
       }
     if (tid < I.n_out) {
       float s = 0.f;
@@ -453,37 +476,36 @@ struct TcTile {
     }
   }
 
-  // sum of per-warpgroup partials in slot k of PART -> FP64 slice at dst[u]
+  // slot k of PART summed over warpgroups and sub-tiles -> FP64 slice at dst[u * stride]
   __device__ void part_flush(int k, double* dst, int stride) {
     if (wg != 0) return;
     for (int h = 0; h < I.H; ++h) {
       const int u = h * 128 + ul;
-      if (u >= I.w) continue;
-      double s = 0.0;
-      for (int w2 = 0; w2 < nwg; ++w2) s += (double)PART(w2, k, u);
-      tc::red_add_f64(dst + (long long)u * stride, s);
+      if (u >= I.wu) continue;
+      tc::red_add_f64(dst + (long long)u * stride, part_sum(k, u));
     }
   }
 
   // Zbar^l = (d compose/dz)^T Abar^l -> ACT(z_buf); db^l += sum_n Zbar_0
   __device__ void adjoint_epilogue(int l, int z_buf, bool abar_from_ub) {
     const float* ub = UB();
-    const int P = I.P;
+    const int P = I.P, Pc = I.Pc;
     for (int h = 0; h < I.H; ++h) {
-      const int u = h * 128 + ul;
+      const int r = h * 128 + ul;
       if (h * 128 + q * 32 >= I.w) continue;
+      const int sub = r / I.wu, u = r - sub * I.wu;
       const float bu = I.params[I.off_b[l - 1] + u];
       float wl[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
       if (abar_from_ub)
-        for (int o = 0; o < I.n_out; ++o) wl[o] = I.params[I.off_W[I.L - 1] + (long long)o * I.w + u];
+        for (int o = 0; o < I.n_out; ++o) wl[o] = I.params[I.off_W[I.L - 1] + (long long)o * I.wu + u];
       float gb = 0.f;
-      for (int q = wg * PPB; q < P; q += nwg * PPB) {
+      for (int g = wg * PPB; g < Pc; g += nwg * PPB) {
         float zv[C][PPB], abv[C][PPB];
 #pragma unroll
-        for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R0(h) + lane_base() + (uint32_t)(blk(c) * P + q), zv[c]);
+        for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R0(h) + lane_base() + (uint32_t)(blk(c) * Pc + g), zv[c]);
         if (!abar_from_ub) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R1(h) + lane_base() + (uint32_t)(blk(c) * P + q), abv[c]);
+          for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R1(h) + lane_base() + (uint32_t)(blk(c) * Pc + g), abv[c]);
         }
         tc::tmem_wait_ld();
         if (abar_from_ub) {
@@ -492,7 +514,7 @@ struct TcTile {
 #pragma unroll
             for (int j = 0; j < PPB; ++j) {
               float s = 0.f;
-              for (int o = 0; o < I.n_out; ++o) s = fmaf(wl[o], ub[(o * C + c) * P + q + j], s);
+              for (int o = 0; o < I.n_out; ++o) s = fmaf(wl[o], ub[(o * C + c) * P + sub * Pc + g + j], s);
               abv[c][j] = s;
             }
         }
@@ -513,26 +535,32 @@ struct TcTile {
           gb += zb[0];
         }
 #pragma unroll
-        for (int c = 0; c < C; ++c) st_bf16<PPB>(ACT(z_buf), u, blk(c) * P + q, zbv[c]);
+        for (int c = 0; c < C; ++c) st_bf16<PPB>(ACT(z_buf), r, blk(c) * Pc + g, zbv[c]);
       }
-      PART(wg, 0, u) = gb;
+      PART(wg, 0, r) = gb;
     }
   }
 
-  // D[R0] (weight gradient block nb of layer l) -> FP64 slice
+  // D[R0] (weight gradient block nb of layer l) -> FP64 slice.  With packed
+  // sub-tiles only the diagonal block of the lane's sub-tile is read: D holds
+  // Zbar A^T over all operand rows, and rows of different sub-tiles belong to
+  // different points.
   __device__ void flush_wgrad(int l, int nb, int NB, double* g) {
     double* gW = g + I.off_W[l - 1];
     for (int h = 0; h < I.H; ++h) {
       if (h * 128 + q * 32 >= I.w) continue;
-      const int j = h * 128 + ul;
-      for (int k0 = wg * 8; k0 < NB; k0 += nwg * 8) {
+      const int r = h * 128 + ul, sub = r / I.wu, j = r - sub * I.wu;
+      const int kcol = I.G > 1 ? sub * I.wu : 0;  // TMEM column of in-unit 0
+      const int kn = I.G > 1 ? I.wu : NB;
+      const int kbase = I.G > 1 ? 0 : nb * NB;
+      for (int k0 = wg * 8; k0 < kn; k0 += nwg * 8) {
         float v[8];
-        tc::tmem_ld8(R0(h) + lane_base() + (uint32_t)k0, v);
+        tc::tmem_ld8(R0(h) + lane_base() + (uint32_t)(kcol + k0), v);
         tc::tmem_wait_ld();
-        const int k = nb * NB + k0;
+        const int k = kbase + k0;
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-          if (k + i < I.w) tc::red_add_f64(gW + (long long)j * I.w + k + i, (double)v[i]);
+          if (k + i < I.wu) tc::red_add_f64(gW + (long long)j * I.wu + k + i, (double)v[i]);
       }
     }
   }
@@ -541,22 +569,24 @@ struct TcTile {
   __device__ void layer1_bwd(bool abar_from_ub) {
     const float* Pm = I.params;
     const float* ub = UB();
-    const int P = I.P;
+    const int P = I.P, Pc = I.Pc, d = I.d;
     for (int h = 0; h < I.H; ++h) {
-      const int u = h * 128 + ul;
+      const int r = h * 128 + ul;
       if (h * 128 + q * 32 >= I.w) continue;
+      const int sub = r / I.wu, u = r - sub * I.wu;
       float w1[3] = {0.f, 0.f, 0.f};
-      for (int i = 0; i < I.d; ++i) w1[i] = Pm[I.off_W[0] + u * I.d + i];
+      for (int i = 0; i < d; ++i) w1[i] = Pm[I.off_W[0] + u * d + i];
       const float b1 = Pm[I.off_b[0] + u];
       float wl[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
       if (abar_from_ub)
-        for (int o = 0; o < I.n_out; ++o) wl[o] = Pm[I.off_W[I.L - 1] + (long long)o * I.w + u];
+        for (int o = 0; o < I.n_out; ++o) wl[o] = Pm[I.off_W[I.L - 1] + (long long)o * I.wu + u];
+      const float* xs = XS() + sub * Pc * d;
       float gw[3] = {0.f, 0.f, 0.f}, gb = 0.f;
-      for (int q = wg * PPB; q < P; q += nwg * PPB) {
+      for (int g = wg * PPB; g < Pc; g += nwg * PPB) {
         float abv[C][PPB];
         if (!abar_from_ub) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R1(h) + lane_base() + (uint32_t)(blk(c) * P + q), abv[c]);
+          for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R1(h) + lane_base() + (uint32_t)(blk(c) * Pc + g), abv[c]);
           tc::tmem_wait_ld();
         } else {
 #pragma unroll
@@ -564,7 +594,7 @@ struct TcTile {
 #pragma unroll
             for (int j = 0; j < PPB; ++j) {
               float s = 0.f;
-              for (int o = 0; o < I.n_out; ++o) s = fmaf(wl[o], ub[(o * C + c) * P + q + j], s);
+              for (int o = 0; o < I.n_out; ++o) s = fmaf(wl[o], ub[(o * C + c) * P + sub * Pc + g + j], s);
               abv[c][j] = s;
             }
         }
@@ -577,7 +607,7 @@ struct TcTile {
             ab[c] = abv[c][j];
           }
           float v = b1;
-          for (int i = 0; i < I.d; ++i) v = fmaf(w1[i], XS()[(q + j) * I.d + i], v);
+          for (int i = 0; i < d; ++i) v = fmaf(w1[i], xs[(g + j) * d + i], v);
           z[0] = v;
 #pragma unroll
           for (int i = 0; i < Cls::D; ++i) {
@@ -587,7 +617,7 @@ struct TcTile {
           tanh_derivs_fast<NP>(z[0], p);
           Cls::adjoint(z, p, ab, zb);
           gb += zb[0];
-          for (int i = 0; i < I.d; ++i) gw[i] = fmaf(zb[0], XS()[(q + j) * I.d + i], gw[i]);
+          for (int i = 0; i < d; ++i) gw[i] = fmaf(zb[0], xs[(g + j) * d + i], gw[i]);
 #pragma unroll
           for (int i = 0; i < Cls::D; ++i) {
             const int fo = Cls::first_order(i);
@@ -595,8 +625,8 @@ struct TcTile {
           }
         }
       }
-      for (int i = 0; i < 3; ++i) PART(wg, i, u) = gw[i];
-      PART(wg, 3, u) = gb;
+      for (int i = 0; i < 3; ++i) PART(wg, i, r) = gw[i];
+      PART(wg, 3, r) = gb;
     }
   }
 
@@ -684,6 +714,7 @@ struct TcTile {
     out_grads(cur);
     __syncthreads();
     out_grads_flush(g);
+    __syncthreads();  // PART is rewritten by the first adjoint epilogue
     const int zb = cur, ain = cur ^ 1;
     for (int l = L - 1; l >= 2; --l) {
       if (l < L - 1) {

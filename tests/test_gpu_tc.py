@@ -180,7 +180,7 @@ def test_tc_store_mode_weight_gradient(name, fam, coefs, widths, domain, N, prec
 @pytest.mark.parametrize("name,fam,coefs,widths,domain,N,prec,tile", [
     ("ks_w64", "ks", dict(c1=1.0, c2=1.0, c4=1.0), [2] + [64] * 5 + [1], [(0, 2 * math.pi), (0, 1)], 700, "bf16", 16),
     ("ns_psi_w128", "ns_psi", dict(nu=0.01), [3] + [128] * 4 + [2], [(0, 1)] * 3, 150, "bf16", 8),
-    ("burgers_w32", "burgers", dict(nu=0.01 / math.pi), [2, 32, 32, 32, 1], DOM2, 333, "bf16", 16),
+    ("burgers_w32", "burgers", dict(nu=0.01 / math.pi), [2, 32, 32, 32, 1], DOM2, 333, "bf16", 32),
     ("allen_cahn_L2", "allen_cahn", dict(eps=1e-4, k=5.0), [2, 128, 1], DOM2, 41, "bf16", 8),
 ], ids=["ks", "ns", "burgers", "ac_L2"])
 def test_tc_two_ctas_per_sm(name, fam, coefs, widths, domain, N, prec, tile):
@@ -218,3 +218,49 @@ def test_tc_two_ctas_rejects_wide_layers():
     with pytest.raises(jet.JetError):
         jet.Plan(sp, [3, 256, 256, 1], "bf16", ctas=2)
     assert jet.Plan(sp, [3, 256, 256, 1], "bf16").info()["ctas_per_sm"] == 1
+
+
+@pytest.mark.parametrize("width,tiles", [(32, (32, 64, 128)), (64, (16, 48, 80))])
+def test_tc_packed_subtiles_any_tile(width, tiles):
+    """Widths 32 and 64 pack 4 or 2 sub-tiles of points into the 128 MMA rows
+    (block-diagonal weights): every tile size the plan accepts gives the same
+    residuals and gradients (up to FP32 summation order), within the oracle
+    bound, including a point count that leaves sub-tiles partly empty."""
+    from paper_2606_29702_gb300 import jet
+    widths = [2, width, width, width, 1]
+    sp, X, layers, src, L, r_ref, g_ref = _setup("burgers", dict(nu=0.01 / math.pi), widths, DOM2, 203)
+    p = _dev(wl.pack(layers))
+    x = _dev(X)
+    outs = []
+    for t in tiles:
+        plan = jet.Plan(sp, widths, "bf16", tile=t)
+        assert plan.info()["tile_points"] == t
+        r, _ = plan.forward(p, x)
+        g, _, _ = plan.backward(p, x)
+        torch.cuda.synchronize()
+        outs.append((r.cpu().numpy(), g.cpu().numpy()))
+        assert rel_l2(outs[-1][0], r_ref) < TOL["bf16"][0] and rel_l2(outs[-1][1], g_ref) < TOL["bf16"][1]
+    for r, g in outs[1:]:
+        assert rel_l2(r, outs[0][0]) < 1e-5 and rel_l2(g, outs[0][1]) < 1e-4
+    # a tile that is not a whole number of sub-tiles of 8 points is refused
+    with pytest.raises(jet.JetError):
+        jet.Plan(sp, widths, "bf16", tile=8 * (128 // width) + 8)
+
+
+@pytest.mark.parametrize("widths,tile,ctas", [([2, 32, 32, 32, 1], 32, 1), ([2, 64, 64, 64, 1], 16, 1),
+                                              ([2, 64, 64, 64, 1], 32, 2), ([2, 128, 128, 1], 8, 1)])
+def test_tc_backward_bitwise_repeatable(widths, tile, ctas):
+    """Per-chunk FP64 gradient slices make repeated calls bitwise identical;
+    a cross-warpgroup race on the partial-sum area would show up here as
+    run-to-run differences (small tiles, all warpgroups active)."""
+    from paper_2606_29702_gb300 import jet, specs
+    sp = specs.burgers(0.01 / math.pi)
+    X = wl.points(DOM2, 999, 5)
+    p = _dev(wl.pack(wl.xavier_layers(widths, 6, bias_std=0.1)))
+    x = _dev(X)
+    plan = jet.Plan(sp, widths, "bf16", tile=tile, ctas=ctas)
+    g0, l0, _ = plan.backward(p, x)
+    for _ in range(4):
+        g, l, _ = plan.backward(p, x)
+        torch.cuda.synchronize()
+        assert torch.equal(g, g0) and float(l) == float(l0)
