@@ -8,6 +8,11 @@ MLP, N = 65536 points uniform on [0, 2pi] x [0, 1], plain FP32 form (the
 configuration the points/s metric is quoted on).  Other precision forms of the
 same workload are timed beside it under "forms".
 
+``--workload ensemble_64`` times the batched form instead: 64 independent
+PINNs (32 Burgers, 32 Allen-Cahn; widths 32/64/128, 3-8 hidden layers, N_i in
+[2048, 65536]) trained together by one persistent BF16 launch per step,
+captured in a CUDA graph and replayed; points/s counts every instance's points.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs an independent replica of the workload (the
 points are independent; no collective on the data path): weak scaling.
@@ -179,46 +184,58 @@ def roofline(form, flops, kernel_ms, peaks, peak_kind):
 
 
 def fp64_alu_peak_tflops(sm_mhz=2070.0, sms=152):
-    """FP64 FMA peak: 152 SMs x 2 FP64 lanes per SM partition quad (64 FP64
-    flops/clk/SM on GB300 per unit count ratio 1:64 of FP32) -- reported for
-    context only."""
+    """FP64 FMA peak: 152 SMs x 2 FP64 FMA per clock x 2 flop x SM clock, the
+    nominal 1.25 TFLOP/s of a GB300."""
     return sms * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
 # ------------------------------------------------------------------ reference
 def run_reference(args, rank, ws):
     """The oracle (FP64 NumPy) as it stands on the host cores, on a bounded
-    sample of the workload per step."""
+    sample of the workload per step (for the ensemble: 32 points of every
+    instance per step)."""
     if rank != 0:
         return
     import oracle
     from oracle import residuals as R
     from paper_2606_29702_gb300 import workloads as wl
-    spec = wl.WORKLOADS[args.workload]
-    S = 256
-    X = wl.points(spec["domain"], S, spec["seed_pts"])
-    layers = wl.xavier_layers(spec["widths"], spec["seed_par"])
-    fam = R.by_name(spec["family"], **spec["coefs"])
-    src = R.helmholtz_source(X, spec["coefs"]["k"])[:, None] if spec["family"] == "helmholtz" else None
-    theta = wl.pack(layers)
-    m = np.zeros_like(theta)
-    v = np.zeros_like(theta)
-    for _ in range(args.warmup):
-        oracle.loss_and_grad(fam, wl.unpack(theta, spec["widths"]), X, source=src)
+    jobs = []  # (residual family, widths, points, packed params, source)
+    if args.workload == "ensemble_64":
+        for ins in wl.ensemble():
+            jobs.append((R.by_name(ins["family"], **ins["coefs"]), ins["widths"], ins["X"][:32],
+                         wl.pack(ins["layers"]), None))
+        widths, sample = "32/64/128, 3-8 hidden layers", "32 points of each of the 64 instances per step"
+    else:
+        spec = wl.WORKLOADS[args.workload]
+        X = wl.points(spec["domain"], 256, spec["seed_pts"])
+        src = R.helmholtz_source(X, spec["coefs"]["k"])[:, None] if spec["family"] == "helmholtz" else None
+        jobs.append((R.by_name(spec["family"], **spec["coefs"]), spec["widths"], X,
+                     wl.pack(wl.xavier_layers(spec["widths"], spec["seed_par"])), src))
+        widths, sample = spec["widths"], "256 of the workload's points per step"
+    S = sum(j[2].shape[0] for j in jobs)
+    state = [(j[3], np.zeros_like(j[3]), np.zeros_like(j[3])) for j in jobs]
+
+    def step(k):
+        for i, (fam, wid, X, _, src) in enumerate(jobs):
+            theta, m, v = state[i]
+            _, _, g = oracle.loss_and_grad(fam, wl.unpack(theta, wid), X, source=src)
+            state[i] = oracle.adam_step(theta, m, v, wl.pack(g), k + 1)
+
+    for k in range(args.warmup):
+        step(k)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        L, _, g = oracle.loss_and_grad(fam, wl.unpack(theta, spec["widths"]), X, source=src)
-        theta, m, v = oracle.adam_step(theta, m, v, wl.pack(g), k + 1)
+        step(args.warmup + k)
     dt = (time.perf_counter() - t0) / args.steps
     cores = _blas_threads()
     val = S / dt
     out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": args.workload, "points_per_step": S, "widths": spec["widths"],
+           "config": {"workload": args.workload, "points_per_step": S, "widths": widths,
                       "note": "FP64 oracle (hyper-dual jets + reverse tape), bounded sample per step"},
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": "%d of the workload's points per step, %d steps" % (S, args.steps)},
+                            "sample": "%s, %d steps" % (sample, args.steps)},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -357,8 +374,95 @@ def time_form(spec, form, X_host, steps, warmup, flush, want_kernel=False, e2e=F
     return out
 
 
+def run_ensemble(args, rank, ws, local):
+    """Batched ensemble: one graph-captured jet_batch_train_step per step."""
+    import torch
+    from paper_2606_29702_gb300 import jet, specs
+    from paper_2606_29702_gb300 import workloads as wl
+    form = args.form or "bf16"
+    insts = wl.ensemble(base_seed=100 + 1000 * rank)
+    dev = torch.device("cuda")
+    plans = [jet.Plan(specs.by_name(i["family"], **i["coefs"]), i["widths"], form) for i in insts]
+    ps = [torch.tensor(wl.pack(i["layers"]), dtype=torch.float32, device=dev) for i in insts]
+    ms_ = [torch.zeros_like(p) for p in ps]
+    vs = [torch.zeros_like(p) for p in ps]
+    xh = [torch.tensor(i["X"], dtype=torch.float32).pin_memory() for i in insts]
+    xs = [x.to(dev) for x in xh]
+    n_pts = sum(i["N"] for i in insts)
+    loss = torch.empty(len(insts), dtype=torch.float64, device=dev)
+    batch = jet.Batch(plans)
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    W = max(args.warmup, 3)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for k in range(W):
+            batch.train_step(ps, ms_, vs, k + 1, 1e-3, xs, loss=loss, stream=s)
+    torch.cuda.synchronize()
+    # one step captured as a CUDA graph (descriptor uploads, weight preparation,
+    # the persistent batched kernel and the batched FP64 reduce + Adam)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        batch.train_step(ps, ms_, vs, W + 1, 1e-3, xs, loss=loss, stream=s)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    barrier(ws)
+    clocks.start()
+    evs = []
+    for _ in range(args.steps):
+        flush_buf.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms_local = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    # end to end: pinned host points in, losses out, every step
+    lh = torch.empty(len(insts), dtype=torch.float64).pin_memory()
+    evs = []
+    for _ in range(args.steps):
+        flush_buf.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for xd, xp in zip(xs, xh):
+            xd.copy_(xp, non_blocking=True)
+        g.replay()
+        lh.copy_(loss, non_blocking=True)
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    barrier(ws)
+    clk = clocks.stop()
+    ms, value = aggregate(ms_local, n_pts, ws)
+    e2e_ms = max_over_ranks(e2e_ms, ws)
+    flops = sum(i["N"] * flops_per_point(i["widths"], 4) for i in insts)
+    peaks, peak_kind = measured_peaks()
+    roof = roofline(form, flops, ms_local, peaks, peak_kind)
+    roof["kernel"] = "batched step (graph replay: weight preparation, persistent tcgen05 kernel, reduce + Adam)"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": W,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "bf16x3": "bf16x3"}[form], "data": "synthetic",
+           "config": {"workload": "ensemble_64", "instances": len(insts), "points_per_replica": n_pts,
+                      "widths": sorted(set(i["widths"][1] for i in insts)),
+                      "depths": [min(len(i["widths"]) - 2 for i in insts), max(len(i["widths"]) - 2 for i in insts)],
+                      "form": form, "l2": "flushed between steps (2x L2 write, outside the per-step events)",
+                      "step": "jet_batch_train_step of all instances, one CUDA graph replay"},
+           "e2e": {"value": ws * n_pts / (e2e_ms * 1e-3), "unit": UNIT,
+                   "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in xh)),
+                   "d2h_bytes_per_step": int(lh.numel() * lh.element_size())},
+           "gpu_launches": (len(insts) + 2) * args.steps, "roofline": roof, "clocks": clk, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def run_ours(args, rank, ws, local):
     import torch
+    if args.workload == "ensemble_64":
+        return run_ensemble(args, rank, ws, local)
     from paper_2606_29702_gb300 import workloads as wl
     spec = dict(wl.WORKLOADS[args.workload])
     if args.n:
