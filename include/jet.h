@@ -73,9 +73,13 @@ typedef enum {
 
 /* plan flags */
 #define JET_FLAG_AUTO_CLOSE 0x1  /* close `needed` downward instead of failing */
-#define JET_FLAG_STORE 0x2       /* jet_forward_residual keeps the hidden z-jets
-                                    (if they fit the budget) for the next
-                                    jet_backward_params on the same inputs */
+#define JET_FLAG_STORE 0x2       /* FP64/FP32 forms: jet_forward_residual keeps
+                                    the hidden z-jets (if they fit the budget)
+                                    for the next jet_backward_params on the
+                                    same inputs.  BF16 forms: the backward pass
+                                    keeps every tile's layer inputs and adjoints
+                                    in HBM (within the budget) and computes the
+                                    weight gradients as one GEMM per layer */
 /* Tile override (used by the autotuner): points per tile of the fused kernel,
  * P = 8 * JET_FLAG_TILE_GET(flags) when nonzero.  The plan rejects a P its
  * kernel cannot run (JET_ERR_UNSUPPORTED); 0 keeps the built-in choice. */
@@ -141,10 +145,14 @@ typedef struct {
  *              (Sec. 2.2: only the required states and their lower-order
  *              chain are propagated).
  *   prec       jet_precision.
- *   mem_budget_bytes  upper bound on plan-owned device memory for the z-jet
- *              store (JET_FLAG_STORE); 0 = no store.  The backward pass always
- *              works in bounded memory by recomputing the jets of each tile
- *              from its layer inputs.
+ *   mem_budget_bytes  upper bound on plan-owned device memory for the store
+ *              of JET_FLAG_STORE; 0 = no store.  Without a store the backward
+ *              pass works in bounded memory by recomputing the jets of each
+ *              tile from its layer inputs.  A BF16 store plan may pick a tile
+ *              that fits shared memory only with the store (one activation
+ *              buffer); its jet_backward_params / jet_train_step then return
+ *              JET_ERR_OOM when N points do not fit the budget, and it cannot
+ *              join a batch (JET_ERR_UNSUPPORTED).
  * On success *out owns device workspace until jet_plan_destroy.
  */
 jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32_t d_in, int32_t n_layers,

@@ -29,6 +29,10 @@ struct TcPlan {
   // packing: G = 128 / wu sub-tiles of Pc points each share the MMA rows
   // (block-diagonal weights); w = G * wu is the width the MMAs see
   int wu = 0, G = 1, Pc = 0;
+  // store-mode plans whose tile only fits with one activation buffer: the
+  // weight gradient always runs as the separate GEMM (never per tile), so
+  // the layer input and its adjoint never need to be in shared memory together
+  bool single_act = false;
   int tmem_cols = 0, ctas_per_sm = 1, grid = 0;
   int nthreads = 512;  // CTA size: 512 (one CTA per SM) or 256 (two)
   size_t smem = 0;
@@ -354,12 +358,12 @@ size_t carve(TcPlan& t, int C, int n_out, int d) {
   t.alo_bytes = lch * (R / 8) * 1024;
   t.o_a0 = (int)off;
   off += t.act_bytes;
-  t.o_a1 = (int)off;
-  off += t.act_bytes;
+  t.o_a1 = t.single_act ? t.o_a0 : (int)off;
+  if (!t.single_act) off += t.act_bytes;
   t.o_alo0 = (int)off;
   off += t.alo_bytes;
-  t.o_alo1 = (int)off;
-  off += t.alo_bytes;
+  t.o_alo1 = t.single_act ? t.o_alo0 : (int)off;
+  if (!t.single_act) off += t.alo_bytes;
   t.o_uo = (int)off;
   off += (size_t)n_out * C * t.P * 4;
   t.o_ub = (int)off;
@@ -414,6 +418,7 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   int best_score = -1;
   TcPlan best = *t;
   const int p8 = JET_FLAG_TILE_GET(flags), want_ctas = JET_FLAG_CTAS_GET(flags);
+  const bool want_store = (flags & JET_FLAG_STORE) && mem_budget > 0 && L >= 3;
   if (want_ctas > 2) {
     delete t;
     return tfail(JET_ERR_INVALID, "JET_FLAG_CTAS takes 0, 1 or 2");
@@ -439,13 +444,17 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
         snprintf(why, sizeof(why), "P=%d: split columns not a multiple of 16", P);
         continue;
       }
-      const size_t sm = carve(c, C, p->n_out, p->d) + 1024;
+      size_t sm = carve(c, C, p->n_out, p->d) + 1024;
+      if (sm > (size_t)(226 * 1024) / ctas && want_store) {
+        c.single_act = true;  // store mode: one activation buffer may be enough
+        sm = carve(c, C, p->n_out, p->d) + 1024;
+      }
       if (sm > (size_t)(226 * 1024) / ctas) {
         snprintf(why, sizeof(why), "P=%d, %d CTA/SM: %zu B of shared memory", P, ctas, sm);
         continue;
       }
       const int NB = c.H == 2 ? 128 : c.w;  // N of the weight-gradient MMA (the MMA width)
-      c.r0w = std::max(c.cols_pad, NB);
+      c.r0w = c.single_act ? c.cols_pad : std::max(c.cols_pad, NB);
       c.r1w = c.cols_pad;
       const int need = c.H * (c.r0w + c.r1w);
       int tm = 32;
@@ -515,7 +524,7 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   }
   *t->h_err = 0;
   t->ws_bytes = b_wh + b_wl + b_wlo + b_gs + b_ls + b_sc;
-  if ((flags & JET_FLAG_STORE) && mem_budget > 0 && L >= 3) {
+  if (want_store) {
     t->wstore_tile_stride = (long long)(L - 2) * (t->act_bytes + t->alo_bytes) + (long long)(L - 2) * t->act_bytes;
     t->wstore_budget = mem_budget;
     if ((long long)(mem_budget / (size_t)t->wstore_tile_stride) > 0) {
@@ -650,6 +659,15 @@ void fill_tc(const jet_plan_s* p, const TcPlan* t, const void* params, const voi
 // budget allows; otherwise the call runs in per-tile mode.  A call that grows
 // it allocates (and cudaFree synchronises): make the first call with the
 // largest N before any stream capture.
+jet_status store_too_small(const TcPlan* t, long long N) {
+  char msg[200];
+  snprintf(msg, sizeof(msg),
+           "this plan's tile keeps one activation buffer and needs the weight-gradient store, which cannot hold "
+           "%lld points within mem_budget (%zu bytes): raise mem_budget or use a smaller tile",
+           N, t->wstore_budget);
+  return tfail(JET_ERR_OOM, msg);
+}
+
 void ensure_store(TcPlan* t, long long N) {
   if (!t->wstore_budget || !t->wg_out || N < 1) return;
   const long long tiles = (N + t->P - 1) / t->P;
@@ -791,6 +809,7 @@ jet_status tc_backward(jet_plan_s* p, TcPlan* t, const void* params, const void*
   if (st != JET_OK) return st;
   TcInst I;
   fill_tc(p, t, params, X, N, source, r_out, I);
+  if (t->single_act && !I.wstore) return store_too_small(t, N);
   st = run(p, t, MODE_FWD_BWD, I, s);
   if (st != JET_OK) return st;
   ReduceJob j;
@@ -816,6 +835,7 @@ jet_status tc_train_step(jet_plan_s* p, TcPlan* t, void* params, void* m, void* 
   if (st != JET_OK) return st;
   TcInst I;
   fill_tc(p, t, params, X, N, source, nullptr, I);
+  if (t->single_act && !I.wstore) return store_too_small(t, N);
   st = run(p, t, MODE_FWD_BWD, I, s);
   if (st != JET_OK) return st;
   ReduceJob j;
@@ -868,6 +888,12 @@ jet_status tc_batch_create(const std::vector<jet_plan_s*>& plans, TcBatch** out)
   b->n = (int)plans.size();
   b->cls = plans[0]->cls;
   long long slices = 0;
+  for (jet_plan_s* p : plans)
+    if (p->tcp->single_act) {
+      delete b;
+      return tfail(JET_ERR_UNSUPPORTED, "a plan whose tile needs the weight-gradient store cannot be batched "
+                                        "(batches flush weight gradients per tile): create it without JET_FLAG_STORE");
+    }
   for (jet_plan_s* p : plans) {
     TcPlan* t = p->tcp;
     b->smem = std::max(b->smem, t->smem);
@@ -962,6 +988,7 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
     I.scratch = b->scratch;
     I.scratch_stride = b->scratch_stride;
     I.slice_shared = 0;  // batches keep one deterministic slice per chunk
+    I.wstore = nullptr;  // and flush weight gradients per tile
     double per_tile = (double)(p->L - 1) * t->w * t->w * t->cols_pad + 2000.0 * t->w * t->P * (p->L - 1);
     for (int c = 0; c < I.n_chunks; ++c) {
       const long long t0 = (long long)c * I.tiles_per_chunk;

@@ -168,7 +168,12 @@ def test_tc_store_mode_weight_gradient(name, fam, coefs, widths, domain, N, prec
     g2, l2, _ = stored.backward(p, x, s)  # second call reuses the store
     torch.cuda.synchronize()
     assert rel_l2(g1.cpu().numpy(), g0.cpu().numpy()) < 1e-4
-    assert torch.equal(g1, g2) and float(l1) == float(l2) == float(l0)
+    # the store plan may take a larger tile (different chunk sums) and wide
+    # nets add into one shared FP64 accumulator (atomic order): equal to FP64
+    # rounding, not bitwise
+    assert rel_l2(g2.cpu().numpy(), g1.cpu().numpy()) < 1e-12
+    assert abs(float(l1) - float(l2)) <= 1e-13 * abs(float(l1))
+    assert abs(float(l1) - float(l0)) <= 1e-12 * abs(float(l0))
     assert rel_l2(g1.cpu().numpy(), g_ref) < TOL[prec][1]
     m = torch.zeros_like(p)
     v = torch.zeros_like(p)
@@ -264,3 +269,26 @@ def test_tc_backward_bitwise_repeatable(widths, tile, ctas):
         g, l, _ = plan.backward(p, x)
         torch.cuda.synchronize()
         assert torch.equal(g, g0) and float(l) == float(l0)
+
+
+def test_tc_single_buffer_store_plan_limits():
+    """A 256-wide store plan takes a 16-point tile that fits shared memory only
+    with one activation buffer: it matches the per-tile plan (covered above),
+    refuses N beyond its store budget with JET_ERR_OOM instead of falling back
+    to a per-tile schedule it cannot run, and cannot join a batch."""
+    from paper_2606_29702_gb300 import jet, specs
+    widths = [3, 256, 256, 256, 256, 1]
+    sp = specs.helmholtz(4 * math.pi)
+    plan = jet.Plan(sp, widths, "bf16", store=True, mem_budget=1 << 20)
+    assert plan.info()["tile_points"] == 16
+    X = wl.points([(-1, 1)] * 3, 200, 1)
+    p = _dev(wl.pack(wl.xavier_layers(widths, 2)))
+    x = _dev(X)
+    s = _dev(specs.helmholtz_source(X, 4 * math.pi))
+    with pytest.raises(jet.JetError, match="JET_ERR_OOM"):
+        plan.backward(p, x, s)
+    r, loss = plan.forward(p, x, s)  # the forward needs no store
+    torch.cuda.synchronize()
+    assert torch.isfinite(r).all()
+    with pytest.raises(jet.JetError, match="cannot be batched"):
+        jet.Batch([plan])
