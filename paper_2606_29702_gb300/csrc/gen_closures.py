@@ -116,6 +116,29 @@ def mono(coef, k, zs, zname="z"):
     return s
 
 
+def factors(coef, k, zs):
+    """Factor strings of one monomial coef * p[k] * prod z[zs]."""
+    f = ["p[%d]" % k] + ["z[%d]" % i for i in zs]
+    if coef != 1:
+        f = ["T(%d)" % coef] + f
+    return f
+
+
+def fma_sum(terms):
+    """Sum of products as a chain of fused multiply-adds: every term after the
+    first adds as jfma(last factor, product of the others, partial sum); a
+    first term is a plain product.  terms = lists of factor strings."""
+    acc = None
+    for fs in terms:
+        if acc is None:
+            acc = "*".join(fs)
+        elif len(fs) == 1:
+            acc = "(%s + %s)" % (acc, fs[0])
+        else:
+            acc = "jfma(%s, %s, %s)" % (fs[-1], "*".join(fs[:-1]), acc)
+    return acc if acc is not None else "T(0)"
+
+
 def emit_class(name, d, chans):
     C = len(chans)
     maxord = max(sum(c) for c in chans)
@@ -139,8 +162,7 @@ def emit_class(name, d, chans):
     # compose
     L.append("  template <class T> static __device__ __forceinline__ void compose(const T* z, const T* p, T* a) {")
     for ai in range(C):
-        expr = " + ".join(mono(c, k, bl) for c, k, bl in terms[ai])
-        L.append("    a[%d] = %s;" % (ai, expr))
+        L.append("    a[%d] = %s;" % (ai, fma_sum([factors(c, k, bl) for c, k, bl in terms[ai]])))
     L.append("  }")
     # tangent
     L.append("  template <class T> static __device__ __forceinline__ void tangent(const T* z, const T* p, const T* v, T* da) {")
@@ -148,8 +170,8 @@ def emit_class(name, d, chans):
         parts = []
         for bi in range(C):
             if J[ai][bi]:
-                parts.append("(%s)*v[%d]" % (" + ".join(mono(c, k, zs) for c, k, zs in J[ai][bi]), bi))
-        L.append("    da[%d] = %s;" % (ai, " + ".join(parts)))
+                parts.append([fma_sum([factors(c, k, zs) for c, k, zs in J[ai][bi]]), "v[%d]" % bi])
+        L.append("    da[%d] = %s;" % (ai, fma_sum(parts)))
     L.append("  }")
     # adjoint
     L.append("  template <class T> static __device__ __forceinline__ void adjoint(const T* z, const T* p, const T* ab, T* zb) {")
@@ -157,8 +179,8 @@ def emit_class(name, d, chans):
         parts = []
         for ai in range(C):
             if J[ai][bi]:
-                parts.append("ab[%d]*(%s)" % (ai, " + ".join(mono(c, k, zs) for c, k, zs in J[ai][bi])))
-        L.append("    zb[%d] = %s;" % (bi, " + ".join(parts) if parts else "T(0)"))
+                parts.append([fma_sum([factors(c, k, zs) for c, k, zs in J[ai][bi]]), "ab[%d]" % ai])
+        L.append("    zb[%d] = %s;" % (bi, fma_sum(parts)))
     L.append("  }")
     L.append("};")
     return "\n".join(L)
@@ -172,6 +194,10 @@ def emit(path):
     out.append("#pragma once")
     out.append("")
     out.append("namespace jet {")
+    out.append("")
+    out.append("// fused multiply-add of the jet algebra; a packed type adds its own overload")
+    out.append("__device__ __forceinline__ float jfma(float a, float b, float c) { return fmaf(a, b, c); }")
+    out.append("__device__ __forceinline__ double jfma(double a, double b, double c) { return fma(a, b, c); }")
     out.append("")
     for name, (d, chans) in CLASSES.items():
         out.append("// %s: d=%d, channels %s" % (name, d, " ".join("".join(str(x) for x in c) for c in chans)))

@@ -72,6 +72,41 @@ __device__ __forceinline__ void tanh_derivs_fast(float z, float* p) {
   if (NP > 5) p[5] = 8.0f * s * (15.0f * a2 * a2 - 15.0f * a2 + 2.0f);
 }
 
+// Two points' values in one register pair: the jet algebra (compose, adjoint)
+// then runs on the packed FP32 instructions of sm_100+, one multiply, add or
+// fused multiply-add for both points.
+struct f2 {
+  float2 v;
+  __device__ __forceinline__ f2() {}
+  __device__ __forceinline__ f2(float s) : v(make_float2(s, s)) {}
+  __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
+  __device__ __forceinline__ explicit f2(float2 x) : v(x) {}
+};
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 jfma(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
+
+// tanh_derivs_fast for two points at once (the exponential and reciprocal
+// per point, the polynomials in a and s packed)
+template <int NP>
+__device__ __forceinline__ void tanh_derivs_fast2(f2 z, f2* p) {
+  float e0, e1, r0, r1;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e0) : "f"(fabsf(z.v.x) * 2.8853900817779268f));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(fabsf(z.v.y) * 2.8853900817779268f));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(1.0f + e0));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(1.0f + e1));
+  const f2 q(2.0f * r0, 2.0f * r1);
+  const f2 a(copysignf(1.0f - q.v.x, z.v.x), copysignf(1.0f - q.v.y, z.v.y));
+  const f2 s = q * jfma(q, f2(-1.0f), f2(2.0f));
+  const f2 a2 = a * a;
+  p[0] = a;
+  if (NP > 1) p[1] = s;
+  if (NP > 2) p[2] = f2(-2.0f) * a * s;
+  if (NP > 3) p[3] = s * jfma(f2(6.0f), a2, f2(-2.0f));
+  if (NP > 4) p[4] = f2(8.0f) * a * s * jfma(f2(-3.0f), a2, f2(2.0f));
+  if (NP > 5) p[5] = f2(8.0f) * s * jfma(a2, jfma(f2(15.0f), a2, f2(-15.0f)), f2(2.0f));
+}
+
 struct alignas(64) TcInst {
   CUtensorMap wmap;    // hidden weights bf16 [L-2][w][w]: dims (in, out, layer), box (64, R_W, 1)
   CUtensorMap wlmap;   // output weights bf16 [n_out][w]: dims (in, out), box (64, 128)
@@ -307,22 +342,28 @@ struct TcTile {
       for (int g = wg * PPF; g < Pc; g += nwg * PPF) {
         float av[C][PPF];
 #pragma unroll
-        for (int j = 0; j < PPF; ++j) {
-          float z[C], p[NP], a[C];
+        for (int j = 0; j < PPF; j += 2) {
+          f2 z[C], p[NP], a[C];
 #pragma unroll
-          for (int c = 0; c < C; ++c) z[c] = 0.f;
-          float v = b1;
-          for (int i = 0; i < d; ++i) v = fmaf(w1[i], xs[(g + j) * d + i], v);
-          z[0] = v;
+          for (int c = 0; c < C; ++c) z[c] = f2(0.f);
+          float v0 = b1, v1 = b1;
+          for (int i = 0; i < d; ++i) {
+            v0 = fmaf(w1[i], xs[(g + j) * d + i], v0);
+            v1 = fmaf(w1[i], xs[(g + j + 1) * d + i], v1);
+          }
+          z[0] = f2(v0, v1);
 #pragma unroll
           for (int i = 0; i < Cls::D; ++i) {
             const int fo = Cls::first_order(i);
-            if (fo >= 0) z[fo] = w1[i];
+            if (fo >= 0) z[fo] = f2(w1[i]);
           }
-          tanh_derivs_fast<NP>(z[0], p);
+          tanh_derivs_fast2<NP>(z[0], p);
           Cls::compose(z, p, a);
 #pragma unroll
-          for (int c = 0; c < C; ++c) av[c][j] = a[c];
+          for (int c = 0; c < C; ++c) {
+            av[c][j] = a[c].v.x;
+            av[c][j + 1] = a[c].v.y;
+          }
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
@@ -347,15 +388,18 @@ struct TcTile {
         tc::tmem_wait_ld();
         float av[C][PPF];
 #pragma unroll
-        for (int j = 0; j < PPF; ++j) {
-          float z[C], p[NP], a[C];
+        for (int j = 0; j < PPF; j += 2) {
+          f2 z[C], p[NP], a[C];
 #pragma unroll
-          for (int c = 0; c < C; ++c) z[c] = zv[c][j];
-          z[0] += bu;
-          tanh_derivs_fast<NP>(z[0], p);
+          for (int c = 0; c < C; ++c) z[c] = f2(zv[c][j], zv[c][j + 1]);
+          z[0] = z[0] + f2(bu);
+          tanh_derivs_fast2<NP>(z[0], p);
           Cls::compose(z, p, a);
 #pragma unroll
-          for (int c = 0; c < C; ++c) av[c][j] = a[c];
+          for (int c = 0; c < C; ++c) {
+            av[c][j] = a[c].v.x;
+            av[c][j + 1] = a[c].v.y;
+          }
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
@@ -520,19 +564,23 @@ struct TcTile {
         }
         float zbv[C][PPB];
 #pragma unroll
-        for (int j = 0; j < PPB; ++j) {
-          float z[C], p[NP], ab[C], zb[C];
+        for (int j = 0; j < PPB; j += 2) {
+          f2 z[C], p[NP], ab[C], zb[C];
 #pragma unroll
           for (int c = 0; c < C; ++c) {
-            z[c] = zv[c][j];
-            ab[c] = abv[c][j];
+            z[c] = f2(zv[c][j], zv[c][j + 1]);
+            ab[c] = f2(abv[c][j], abv[c][j + 1]);
           }
-          z[0] += bu;
-          tanh_derivs_fast<NP>(z[0], p);
+          z[0] = z[0] + f2(bu);
+          tanh_derivs_fast2<NP>(z[0], p);
           Cls::adjoint(z, p, ab, zb);
 #pragma unroll
-          for (int c = 0; c < C; ++c) zbv[c][j] = zb[c];
-          gb += zb[0];
+          for (int c = 0; c < C; ++c) {
+            zbv[c][j] = zb[c].v.x;
+            zbv[c][j + 1] = zb[c].v.y;
+          }
+          gb += zb[0].v.x;
+          gb += zb[0].v.y;
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) st_bf16<PPB>(ACT(z_buf), r, blk(c) * Pc + g, zbv[c]);
@@ -599,29 +647,39 @@ struct TcTile {
             }
         }
 #pragma unroll
-        for (int j = 0; j < PPB; ++j) {
-          float z[C], p[NP], ab[C], zb[C];
+        for (int j = 0; j < PPB; j += 2) {
+          f2 z[C], p[NP], ab[C], zb[C];
 #pragma unroll
           for (int c = 0; c < C; ++c) {
-            z[c] = 0.f;
-            ab[c] = abv[c][j];
+            z[c] = f2(0.f);
+            ab[c] = f2(abv[c][j], abv[c][j + 1]);
           }
-          float v = b1;
-          for (int i = 0; i < d; ++i) v = fmaf(w1[i], xs[(g + j) * d + i], v);
-          z[0] = v;
+          float v0 = b1, v1 = b1;
+          for (int i = 0; i < d; ++i) {
+            v0 = fmaf(w1[i], xs[(g + j) * d + i], v0);
+            v1 = fmaf(w1[i], xs[(g + j + 1) * d + i], v1);
+          }
+          z[0] = f2(v0, v1);
 #pragma unroll
           for (int i = 0; i < Cls::D; ++i) {
             const int fo = Cls::first_order(i);
-            if (fo >= 0) z[fo] = w1[i];
+            if (fo >= 0) z[fo] = f2(w1[i]);
           }
-          tanh_derivs_fast<NP>(z[0], p);
+          tanh_derivs_fast2<NP>(z[0], p);
           Cls::adjoint(z, p, ab, zb);
-          gb += zb[0];
-          for (int i = 0; i < d; ++i) gw[i] = fmaf(zb[0], xs[(g + j) * d + i], gw[i]);
+          gb += zb[0].v.x;
+          gb += zb[0].v.y;
+          for (int i = 0; i < d; ++i) {
+            gw[i] = fmaf(zb[0].v.x, xs[(g + j) * d + i], gw[i]);
+            gw[i] = fmaf(zb[0].v.y, xs[(g + j + 1) * d + i], gw[i]);
+          }
 #pragma unroll
           for (int i = 0; i < Cls::D; ++i) {
             const int fo = Cls::first_order(i);
-            if (fo >= 0) gw[i] += zb[fo];
+            if (fo >= 0) {
+              gw[i] += zb[fo].v.x;
+              gw[i] += zb[fo].v.y;
+            }
           }
         }
       }
