@@ -593,8 +593,41 @@ struct TcTile {
   // sub-tiles only the diagonal block of the lane's sub-tile is read: D holds
   // Zbar A^T over all operand rows, and rows of different sub-tiles belong to
   // different points.
-  __device__ void flush_wgrad(int l, int nb, int NB, double* g) {
+  __device__ void flush_wgrad(int l, int nb, int NB, double* g, unsigned char* stage) {
     double* gW = g + I.off_W[l - 1];
+    if (I.G > 1) {
+      // Sub-tiles 1..G-1 park their diagonal blocks in shared memory (the
+      // adjoint buffer, free once the weight-gradient MMA has completed);
+      // sub-tile 0 adds them in FP32 and flushes one FP64 add per weight.
+      // Called by every thread (barrier inside); packed plans have H == 1.
+      float* stg = reinterpret_cast<float*>(stage);
+      const int wu = I.wu, sub = ul / wu, j = ul - sub * wu;
+      if (sub > 0)
+        for (int k0 = wg * 8; k0 < wu; k0 += nwg * 8) {
+          float v[8];
+          tc::tmem_ld8(R0(0) + lane_base() + (uint32_t)(sub * wu + k0), v);
+          tc::tmem_wait_ld();
+          // [block][column][row]: the lanes (rows) of a warp store 32
+          // consecutive floats per column, conflict-free
+          float* dst = stg + ((sub - 1) * wu + k0) * wu + j;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) dst[i * wu] = v[i];
+        }
+      __syncthreads();
+      if (sub == 0)
+        for (int k0 = wg * 8; k0 < wu; k0 += nwg * 8) {
+          float v[8];
+          tc::tmem_ld8(R0(0) + lane_base() + (uint32_t)k0, v);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            float t = v[i];
+            for (int o = 1; o < I.G; ++o) t += stg[((o - 1) * wu + k0 + i) * wu + j];
+            tc::red_add_f64(gW + (long long)j * wu + k0 + i, (double)t);
+          }
+        }
+      return;
+    }
     for (int h = 0; h < I.H; ++h) {
       if (h * 128 + q * 32 >= I.w) continue;
       const int r = h * 128 + ul, sub = r / I.wu, j = r - sub * I.wu;
@@ -823,7 +856,7 @@ struct TcTile {
       }
       if (!wait(bar_mma, ph_mma, 64)) break;
       tc::tc_fence_after();
-      flush_wgrad(l, 0, NB, g);
+      flush_wgrad(l, 0, NB, g, ACT(zb));
       for (int nb = 1; nb < nblk; ++nb) {
         sync();
         if (tid == 0) {
@@ -832,7 +865,7 @@ struct TcTile {
         }
         if (!wait(bar_mma, ph_mma, 65)) break;
         tc::tc_fence_after();
-        flush_wgrad(l, nb, NB, g);
+        flush_wgrad(l, nb, NB, g, ACT(zb));
       }
       sync();
     }
