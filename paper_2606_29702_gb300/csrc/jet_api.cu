@@ -295,7 +295,8 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
   for (int l = 1; l < n_layers; ++l) wmax = std::max(wmax, widths[l]);
   const int p8 = JET_FLAG_TILE_GET(flags);
   p->P = p8 ? 8 * p8 : tile_points(p->C, wmax, p->fp64);
-  p->pitch = pitch_for(simt_point_stride(p->C) * p->P, p->fp64);
+  p->S = simt_point_stride(p->C, p->P);
+  p->pitch = pitch_for(p->S * p->P, p->fp64);
   p->smem = smem_bytes(p->C, p->P, p->pitch, wmax, n_out, d_in, p->elem);
   cudaDeviceProp prop;
   cudaError_t e = cudaGetDeviceProperties(&prop, p->device);
@@ -438,6 +439,7 @@ void fill_instance(const jet_plan_s* p, const void* params, const void* X, long 
   for (int m = 0; m < I.n_terms; ++m) I.terms[m] = p->terms[m];
   I.P = p->P;
   I.pitch = p->pitch;
+  I.S = p->S;
   I.n_tiles = (N + p->P - 1) / p->P;
   long long chunks = std::min<long long>(std::max<long long>(I.n_tiles, 1), max_chunks);
   I.tiles_per_chunk = (int)((I.n_tiles + chunks - 1) / chunks);

@@ -49,7 +49,8 @@ struct DevInstance {
   DevTerm terms[kMaxTerms];
   // tiling
   int P;               // points per tile
-  int pitch;           // smem row pitch (elements) of a jet buffer, >= C * P
+  int pitch;           // smem row pitch (elements) of a jet buffer, >= S * P
+  int S;               // point stride within a jet row (SIMT forms)
   long long n_tiles;
   int tiles_per_chunk;
   int n_chunks;
@@ -76,9 +77,14 @@ struct SimtArgs {
 };
 
 constexpr int kSimtThreads = 256;
-// Point stride of a SIMT shared-memory jet row [unit][n * S + alpha]: odd, so
-// that lanes walking points n hit distinct banks.
-__host__ __device__ constexpr int simt_point_stride(int C) { return C | 1; }
+// Point stride S of a SIMT shared-memory jet row [unit][n * S + alpha]: the
+// lanes of a warp walk min(P, 32) points and must hit distinct banks, so S = C
+// when C's power-of-two factor times those lanes fits in 32 banks (C = 6 at
+// P = 16), else the odd C | 1 (pad columns stay zero).
+inline int simt_point_stride(int C, int P) {
+  const int lanes = P < 32 ? P : 32;
+  return (C & -C) * lanes <= 32 ? C : (C | 1);
+}
 // elements of the SIMT weight workspace: transposed copy, then aligned copy
 __host__ __device__ inline long long weight_copy_offset(long long n_params) { return (n_params + 3) & ~3LL; }
 __host__ __device__ inline long long weight_ws_elems(long long n_params) { return 2 * weight_copy_offset(n_params); }

@@ -198,10 +198,12 @@ extern "C" jet_status jet_backward_params_noalloc(const jet_residual_spec* spec,
   // tiling: same rule as the plan path
   const int TP = fp64 ? 2 : 4;
   const int P = TP * (kSimtThreads / wmax > 0 ? kSimtThreads / wmax : 1);
-  int pitch = simt_point_stride(C) * P;
+  const int S = simt_point_stride(C, P);
+  int pitch = S * P;
   while (pitch % (fp64 ? 16 : 32) != (fp64 ? 2 : 4)) ++pitch;
   I.P = P;
   I.pitch = pitch;
+  I.S = S;
   I.n_tiles = (N + P - 1) / P;
   const size_t smem = simt_smem_bytes(C, P, pitch, wmax, n_out, d_in, elem);
   long long jet_elems = 0;

@@ -25,7 +25,7 @@ struct jet_plan_s {
   bool has_source = false;
   long long n_params = 0;
   std::vector<long long> off_W, off_b;
-  int P = 0, pitch = 0;
+  int P = 0, pitch = 0, S = 0;
   size_t smem = 0;
   int grid = 0, ctas_per_sm = 0;
   size_t elem = 4;

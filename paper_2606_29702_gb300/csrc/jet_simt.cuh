@@ -30,6 +30,7 @@
 #pragma once
 
 #include "jet_closures_gen.h"
+#include "jet_f2.cuh"
 #include "jet_internal.h"
 
 namespace jet {
@@ -97,7 +98,6 @@ struct SimtTile {
   static constexpr int TP = Vec<T>::N;
   static constexpr int NT = kSimtThreads;
   static constexpr int RU = TP;  // consecutive units per thread
-  static constexpr int S = simt_point_stride(C);  // row stride of one point
 
   const DevInstance& I;
   const SimtArgs& A;
@@ -106,7 +106,7 @@ struct SimtTile {
   T* UB;     // output adjoints [n_out*C][P]
   T* XS;     // tile points [P][d]
   double* RED;
-  int P, pitch, wmax;
+  int P, pitch, wmax, S;  // S: point stride within a jet row
   const T* params;
   const T* Wt;  // transposed weights [in][out] per layer
   const T* Wc;  // aligned copy of the packed parameters
@@ -114,6 +114,7 @@ struct SimtTile {
   __device__ SimtTile(const DevInstance& I_, const SimtArgs& A_, unsigned char* smem) : I(I_), A(A_) {
     P = I.P;
     pitch = I.pitch;
+    S = I.S;
     wmax = 0;
     for (int l = 1; l < I.L; ++l) wmax = max(wmax, I.widths[l]);
     T* base = reinterpret_cast<T*>(smem);
@@ -142,6 +143,29 @@ struct SimtTile {
     for (int k = 1; k < l; ++k) off += (long long)C * P * I.widths[k];
     if (to_store) return reinterpret_cast<T*>(I.store) + tile * I.store_tile_stride + off;
     return reinterpret_cast<T*>(A.scratch) + (long long)blockIdx.x * A.scratch_stride + off;
+  }
+
+  // acc[r][c] += w[r] * a[c] for RU units and C channels.  FP32: channel
+  // pairs use the packed FMA, with the unit's weight in both halves.
+  static __device__ __forceinline__ void rank1(T (&acc)[RU][C], const T* w, const T* a) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int r = 0; r < RU; ++r) {
+        const f2 wr(w[r]);
+#pragma unroll
+        for (int c = 0; c + 1 < C; c += 2) {
+          const f2 s = jfma(wr, f2(a[c], a[c + 1]), f2(acc[r][c], acc[r][c + 1]));
+          acc[r][c] = s.v.x;
+          acc[r][c + 1] = s.v.y;
+        }
+        if (C & 1) acc[r][C - 1] = fma(w[r], a[C - 1], acc[r][C - 1]);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < RU; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[r][c] = fma(w[r], a[c], acc[r][c]);
+    }
   }
 
   // ---------------------------------------------------------------- forward
@@ -213,10 +237,7 @@ struct SimtTile {
         vldg<T>(wp, wv);
 #pragma unroll
         for (int c = 0; c < C; ++c) av[c] = ap[c];
-#pragma unroll
-        for (int r = 0; r < RU; ++r)
-#pragma unroll
-          for (int c = 0; c < C; ++c) acc[r][c] = fma(wv[r], av[c], acc[r][c]);
+        rank1(acc, wv, av);
       }
 #pragma unroll
       for (int r = 0; r < RU; ++r) {
@@ -319,19 +340,35 @@ struct SimtTile {
     const int L = I.L, wi = I.widths[L - 1], no = I.n_out;
     const T* WL = W(L);
     const int ncol = C * P;
-    for (int it = threadIdx.x; it < wi * ncol; it += NT) {
-      const int k = it / ncol, col = it % ncol;  // col = alpha * P + n
-      T s = T(0);
-      for (int o = 0; o < no; ++o) s = fma(WL[o * wi + k], UB[o * ncol + col], s);
-      abar[k * pitch + (col % P) * S + col / P] = s;
-    }
-    for (int it = threadIdx.x; it < no * wi; it += NT) {
-      const int o = it / wi, k = it % wi;
-      T s = T(0);
-      for (int n = 0; n < P; ++n)
+    // Abar[k][n*S + c], one (unit, point) per item with all channels
+    for (int it = threadIdx.x; it < wi * P; it += NT) {
+      const int n = it % P, k = it / P;
+      T s[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) s = fma(UB[o * ncol + c * P + n], a_last[k * pitch + n * S + c], s);
-      atomicAdd(g + I.off_W[L - 1] + o * wi + k, (double)s);
+      for (int c = 0; c < C; ++c) s[c] = T(0);
+      for (int o = 0; o < no; ++o) {
+        const T w = WL[o * wi + k];
+#pragma unroll
+        for (int c = 0; c < C; ++c) s[c] = fma(w, UB[o * ncol + c * P + n], s[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) abar[k * pitch + n * S + c] = s[c];
+    }
+    // dW^L[o][k]: four lanes share a weight, each summing a quarter of the
+    // points; the partials combine by shuffles in a fixed order
+    // (the loop runs whole warps: every lane of a warp reaches the shuffles)
+    const int items = 4 * no * wi, items_w = (items + 31) & ~31;
+    for (int it = threadIdx.x; it < items_w; it += NT) {
+      const bool act = it < items;
+      const int part = it & 3, ok = it >> 2, o = act ? ok / wi : 0, k = act ? ok % wi : 0;
+      T s = T(0);
+      if (act)
+        for (int n = part; n < P; n += 4)
+#pragma unroll
+          for (int c = 0; c < C; ++c) s = fma(UB[o * ncol + c * P + n], a_last[k * pitch + n * S + c], s);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      if (act && part == 0) atomicAdd(g + I.off_W[L - 1] + o * wi + k, (double)s);
     }
     for (int o = threadIdx.x; o < no; o += NT) {
       T s = T(0);
@@ -427,10 +464,7 @@ struct SimtTile {
         vldg<T>(wp, wv);
 #pragma unroll
         for (int c = 0; c < C; ++c) zv[c] = zp[c];
-#pragma unroll
-        for (int i = 0; i < RU; ++i)
-#pragma unroll
-          for (int c = 0; c < C; ++c) acc[i][c] = fma(wv[i], zv[c], acc[i][c]);
+        rank1(acc, wv, zv);
       }
 #pragma unroll
       for (int i = 0; i < RU; ++i)

@@ -72,20 +72,6 @@ __device__ __forceinline__ void tanh_derivs_fast(float z, float* p) {
   if (NP > 5) p[5] = 8.0f * s * (15.0f * a2 * a2 - 15.0f * a2 + 2.0f);
 }
 
-// Two points' values in one register pair: the jet algebra (compose, adjoint)
-// then runs on the packed FP32 instructions of sm_100+, one multiply, add or
-// fused multiply-add for both points.
-struct f2 {
-  float2 v;
-  __device__ __forceinline__ f2() {}
-  __device__ __forceinline__ f2(float s) : v(make_float2(s, s)) {}
-  __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
-  __device__ __forceinline__ explicit f2(float2 x) : v(x) {}
-};
-__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
-__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
-__device__ __forceinline__ f2 jfma(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
-
 // tanh_derivs_fast for two points at once (the exponential and reciprocal
 // per point, the polynomials in a and s packed)
 template <int NP>
