@@ -57,6 +57,21 @@ __device__ __forceinline__ void tanh_derivs(T z, T* p) {
   if (NP > 5) p[5] = T(8) * s * (T(15) * a2 * a2 - T(15) * a2 + T(2));
 }
 
+// tanh_derivs of two values in a packed pair (accurate tanhf per value, the
+// derivative polynomials in a and s packed)
+template <int NP>
+__device__ __forceinline__ void tanh_derivs_pair(f2 z, f2* p) {
+  const f2 a(tanhf(z.v.x), tanhf(z.v.y));
+  const f2 a2 = a * a;
+  const f2 s = jfma(f2(-1.0f), a2, f2(1.0f));
+  p[0] = a;
+  if (NP > 1) p[1] = s;
+  if (NP > 2) p[2] = f2(-2.0f) * a * s;
+  if (NP > 3) p[3] = s * jfma(f2(6.0f), a2, f2(-2.0f));
+  if (NP > 4) p[4] = f2(8.0f) * a * s * jfma(f2(-3.0f), a2, f2(2.0f));
+  if (NP > 5) p[5] = f2(8.0f) * s * jfma(a2, jfma(f2(15.0f), a2, f2(-15.0f)), f2(2.0f));
+}
+
 template <class T>
 __device__ __forceinline__ void vload(const T* p, T* out) {
   using V = typename Vec<T>::type;
@@ -239,20 +254,45 @@ struct SimtTile {
         for (int c = 0; c < C; ++c) av[c] = ap[c];
         rank1(acc, wv, av);
       }
+      if constexpr (sizeof(T) == 4) {
 #pragma unroll
-      for (int r = 0; r < RU; ++r) {
-        const int u = u0 + r;
-        T z[C], p[NP], a[C];
+        for (int r = 0; r < RU; r += 2) {
+          const int u = u0 + r;
+          f2 z[C], p[NP], a[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) z[c] = acc[r][c];
-        z[0] += bl[u];
-        tanh_derivs<T, NP>(z[0], p);
-        Cls::compose(z, p, a);
+          for (int c = 0; c < C; ++c) z[c] = f2(acc[r][c], acc[r + 1][c]);
+          z[0] = z[0] + f2(bl[u], bl[u + 1]);
+          tanh_derivs_pair<NP>(z[0], p);
+          Cls::compose(z, p, a);
 #pragma unroll
-        for (int c = 0; c < C; ++c) out[u * pitch + n * S + c] = a[c];
-        if (zdst) {
+          for (int c = 0; c < C; ++c) {
+            out[u * pitch + n * S + c] = a[c].v.x;
+            out[(u + 1) * pitch + n * S + c] = a[c].v.y;
+          }
+          if (zdst) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) __stcg(zdst + (long long)u * CP + c * P + n, z[c]);
+            for (int c = 0; c < C; ++c) {
+              __stcg(zdst + (long long)u * CP + c * P + n, z[c].v.x);
+              __stcg(zdst + (long long)(u + 1) * CP + c * P + n, z[c].v.y);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+          const int u = u0 + r;
+          T z[C], p[NP], a[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) z[c] = acc[r][c];
+          z[0] += bl[u];
+          tanh_derivs<T, NP>(z[0], p);
+          Cls::compose(z, p, a);
+#pragma unroll
+          for (int c = 0; c < C; ++c) out[u * pitch + n * S + c] = a[c];
+          if (zdst) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) __stcg(zdst + (long long)u * CP + c * P + n, z[c]);
+          }
         }
       }
     }
@@ -269,13 +309,29 @@ struct SimtTile {
       for (int r = 0; r < RU; ++r)
 #pragma unroll
         for (int c = 0; c < C; ++c) zz[r][c] = __ldcg(zsrc + (long long)(u0 + r) * CP + c * P + n);
+      if constexpr (sizeof(T) == 4) {
 #pragma unroll
-      for (int r = 0; r < RU; ++r) {
-        T p[NP], a[C];
-        tanh_derivs<T, NP>(zz[r][0], p);
-        Cls::compose(zz[r], p, a);
+        for (int r = 0; r < RU; r += 2) {
+          f2 z[C], p[NP], a[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) out[(u0 + r) * pitch + n * S + c] = a[c];
+          for (int c = 0; c < C; ++c) z[c] = f2(zz[r][c], zz[r + 1][c]);
+          tanh_derivs_pair<NP>(z[0], p);
+          Cls::compose(z, p, a);
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            out[(u0 + r) * pitch + n * S + c] = a[c].v.x;
+            out[(u0 + r + 1) * pitch + n * S + c] = a[c].v.y;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+          T p[NP], a[C];
+          tanh_derivs<T, NP>(zz[r][0], p);
+          Cls::compose(zz[r], p, a);
+#pragma unroll
+          for (int c = 0; c < C; ++c) out[(u0 + r) * pitch + n * S + c] = a[c];
+        }
       }
     }
   }
@@ -388,16 +444,37 @@ struct SimtTile {
       for (int r = 0; r < RU; ++r)
 #pragma unroll
         for (int c = 0; c < C; ++c) zz[r][c] = __ldcg(zsrc + (long long)(u0 + r) * CP + c * P + n);
+      if constexpr (sizeof(T) == 4) {
+        // FP32: units (r, r+1) in packed pairs
 #pragma unroll
-      for (int r = 0; r < RU; ++r) {
-        const int u = u0 + r;
-        T p[NP], ab[C], zb[C];
+        for (int r = 0; r < RU; r += 2) {
+          const int u = u0 + r;
+          f2 z[C], p[NP], ab[C], zb[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) ab[c] = abar[u * pitch + n * S + c];
-        tanh_derivs<T, NP>(zz[r][0], p);
-        Cls::adjoint(zz[r], p, ab, zb);
+          for (int c = 0; c < C; ++c) {
+            z[c] = f2(zz[r][c], zz[r + 1][c]);
+            ab[c] = f2(abar[u * pitch + n * S + c], abar[(u + 1) * pitch + n * S + c]);
+          }
+          tanh_derivs_pair<NP>(z[0], p);
+          Cls::adjoint(z, p, ab, zb);
 #pragma unroll
-        for (int c = 0; c < C; ++c) zbar[u * pitch + n * S + c] = zb[c];
+          for (int c = 0; c < C; ++c) {
+            zbar[u * pitch + n * S + c] = zb[c].v.x;
+            zbar[(u + 1) * pitch + n * S + c] = zb[c].v.y;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+          const int u = u0 + r;
+          T p[NP], ab[C], zb[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) ab[c] = abar[u * pitch + n * S + c];
+          tanh_derivs<T, NP>(zz[r][0], p);
+          Cls::adjoint(zz[r], p, ab, zb);
+#pragma unroll
+          for (int c = 0; c < C; ++c) zbar[u * pitch + n * S + c] = zb[c];
+        }
       }
     }
   }
@@ -411,22 +488,50 @@ struct SimtTile {
     for (int it = threadIdx.x; it < (wo / 4) * nkb; it += NT) {
       const int kb = it % nkb, ub = it / nkb;
       T acc[4][4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int s = 0; s < 4; ++s) acc[r][s] = T(0);
-      for (int col = 0; col < ncol; col += TP) {
-        T zv[4][TP], av[4][TP];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) vload<T>(zbar + (ub * 4 + r) * pitch + col, zv[r]);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) vload<T>(aprev + (kb + s * nkb) * pitch + col, av[s]);
+      if constexpr (sizeof(T) == 4) {
+        // FP32: even and odd columns accumulate in the two halves of a
+        // packed pair (the 16-byte loads deliver the pairs), summed at the end
+        f2 ap2[4][4];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int s = 0; s < 4; ++s)
+          for (int s = 0; s < 4; ++s) ap2[r][s] = f2(0.f);
+        for (int col = 0; col < ncol; col += TP) {
+          T zv[4][TP], av[4][TP];
 #pragma unroll
-            for (int j = 0; j < TP; ++j) acc[r][s] = fma(zv[r][j], av[s][j], acc[r][s]);
+          for (int r = 0; r < 4; ++r) vload<T>(zbar + (ub * 4 + r) * pitch + col, zv[r]);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) vload<T>(aprev + (kb + s * nkb) * pitch + col, av[s]);
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+              for (int j = 0; j < TP; j += 2)
+                ap2[r][s] = jfma(f2(zv[r][j], zv[r][j + 1]), f2(av[s][j], av[s][j + 1]), ap2[r][s]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int s = 0; s < 4; ++s) acc[r][s] = ap2[r][s].v.x + ap2[r][s].v.y;
+      } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int s = 0; s < 4; ++s) acc[r][s] = T(0);
+        for (int col = 0; col < ncol; col += TP) {
+          T zv[4][TP], av[4][TP];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) vload<T>(zbar + (ub * 4 + r) * pitch + col, zv[r]);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) vload<T>(aprev + (kb + s * nkb) * pitch + col, av[s]);
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+              for (int j = 0; j < TP; ++j) acc[r][s] = fma(zv[r][j], av[s][j], acc[r][s]);
+        }
       }
       // fire-and-forget FP64 adds: every slice element belongs to one thread,
       // which adds the tiles in order, so the sums stay deterministic
