@@ -579,13 +579,40 @@ struct TcTile {
   // sub-tiles only the diagonal block of the lane's sub-tile is read: D holds
   // Zbar A^T over all operand rows, and rows of different sub-tiles belong to
   // different points.
+  // FP64 adds of a 32-row x 8-column block of the weight gradient (row
+  // row0 + lane, columns k .. k+7, values v) with coalesced addresses: the
+  // warp parks the block in its 1 KB of stg (row-major 32 x 8) and re-reads
+  // it with lanes walking the columns, so every add instruction covers four
+  // contiguous 64-byte runs instead of 32 rows.
+  __device__ void red_block(float* stg, const float* v, int row0, int k, double* gW) const {
+    const int lane = tid & 31;
+    float4* d4 = reinterpret_cast<float4*>(stg + lane * 8);
+    d4[0] = make_float4(v[0], v[1], v[2], v[3]);
+    d4[1] = make_float4(v[4], v[5], v[6], v[7]);
+    __syncwarp();
+    const int col = lane & 7;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int row = t * 4 + (lane >> 3);
+      if (k + col < I.wu) tc::red_add_f64(gW + (long long)(row0 + row) * I.wu + k + col, (double)stg[row * 8 + col]);
+    }
+    __syncwarp();
+  }
+
+  // D[R0] (weight gradient block nb of layer l) -> FP64 slice.  With packed
+  // sub-tiles only the diagonal block of the lane's sub-tile is read: D holds
+  // Zbar A^T over all operand rows, and rows of different sub-tiles belong to
+  // different points.  Called by every thread (barriers inside); PART is free
+  // here and serves as each warp's 1 KB staging area.
   __device__ void flush_wgrad(int l, int nb, int NB, double* g, unsigned char* stage) {
     double* gW = g + I.off_W[l - 1];
+    float* wst = part + warp * 256;  // this warp's staging block
+    __syncthreads();                 // PART may still be read by the bias flush
     if (I.G > 1) {
       // Sub-tiles 1..G-1 park their diagonal blocks in shared memory (the
       // adjoint buffer, free once the weight-gradient MMA has completed);
       // sub-tile 0 adds them in FP32 and flushes one FP64 add per weight.
-      // Called by every thread (barrier inside); packed plans have H == 1.
+      // Packed plans have H == 1.
       float* stg = reinterpret_cast<float*>(stage);
       const int wu = I.wu, sub = ul / wu, j = ul - sub * wu;
       if (sub > 0)
@@ -606,28 +633,20 @@ struct TcTile {
           tc::tmem_ld8(R0(0) + lane_base() + (uint32_t)k0, v);
           tc::tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            float t = v[i];
-            for (int o = 1; o < I.G; ++o) t += stg[((o - 1) * wu + k0 + i) * wu + j];
-            tc::red_add_f64(gW + (long long)j * wu + k0 + i, (double)t);
-          }
+          for (int i = 0; i < 8; ++i)
+            for (int o = 1; o < I.G; ++o) v[i] += stg[((o - 1) * wu + k0 + i) * wu + j];
+          red_block(wst, v, j - (tid & 31), k0, gW);
         }
       return;
     }
     for (int h = 0; h < I.H; ++h) {
-      if (h * 128 + q * 32 >= I.w) continue;
-      const int r = h * 128 + ul, sub = r / I.wu, j = r - sub * I.wu;
-      const int kcol = I.G > 1 ? sub * I.wu : 0;  // TMEM column of in-unit 0
-      const int kn = I.G > 1 ? I.wu : NB;
-      const int kbase = I.G > 1 ? 0 : nb * NB;
-      for (int k0 = wg * 8; k0 < kn; k0 += nwg * 8) {
+      if (h * 128 + q * 32 >= I.w) continue;  // warp-uniform
+      const int row0 = h * 128 + q * 32;     // first weight-gradient row of this warp
+      for (int k0 = wg * 8; k0 < NB; k0 += nwg * 8) {
         float v[8];
-        tc::tmem_ld8(R0(h) + lane_base() + (uint32_t)(kcol + k0), v);
+        tc::tmem_ld8(R0(h) + lane_base() + (uint32_t)k0, v);
         tc::tmem_wait_ld();
-        const int k = kbase + k0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          if (k + i < I.wu) tc::red_add_f64(gW + (long long)j * I.wu + k + i, (double)v[i]);
+        red_block(wst, v, row0, nb * NB + k0, gW);
       }
     }
   }
