@@ -19,6 +19,7 @@ points are independent; no collective on the data path): weak scaling.
 """
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -167,19 +168,52 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def roofline(form, flops, kernel_ms, peaks, peak_kind):
+# DRAM bytes (read + write) of one launch of the dominant kernel, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the same workload and
+# form; (workload, form) -> (bytes per launch, hash of the kernel sources the
+# counters were taken on).  A different hash (the kernels changed since) gives
+# null.  The Helmholtz entry was captured at N = 32768 and scaled by the point
+# count (its traffic is the per-tile store, proportional to N).
+TRAFFIC = {
+    ("ks_2x64x5", "fp32"): (9756928 + 807334144, "12333ac7561a7e7b"),
+    ("ks_2x64x5", "bf16"): (885504 + 9101056, "12333ac7561a7e7b"),
+    ("ks_2x64x5", "bf16x3"): (1018880 + 15339264, "12333ac7561a7e7b"),
+    ("ks_2x64x5", "fp64"): (5640448 + 520318720, "12333ac7561a7e7b"),
+    ("ns_psi_3x128x6", "bf16"): (4340224 + 41560320, "12333ac7561a7e7b"),
+    ("helmholtz_3x256x8", "bf16"): ((314044928 + 1863854848) * 32, "12333ac7561a7e7b"),
+    ("ensemble_64", "bf16"): (2783134976 + 8973665024, "12333ac7561a7e7b"),
+}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2606_29702_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".py")) and name != "jet_closures_gen.h":
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(workload, form):
+    e = TRAFFIC.get((workload, form))
+    return e[0] if e is not None and e[1] == kernel_source_hash() else None
+
+
+def roofline(form, flops, kernel_ms, peaks, peak_kind, traffic=None):
     """Roofline of the dominant kernel: algorithmic jet-GEMM flops / its event time."""
     achieved = flops / (kernel_ms * 1e-3) / 1e12
     if form in ("fp32", "fp64"):
         peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0)) if form == "fp32" else \
             fp64_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "fused SIMT jet kernel (%s)" % form,
+                "traffic": traffic, "kernel": "fused SIMT jet kernel (%s)" % form,
                 "peak_kind": "derived: 152 SM x %s lanes x 2 flop x max clock" % ("128 FP32" if form == "fp32"
                                                                                  else "2 FP64")}
     peak = peaks["bf16_tflops"] * (0.5 if form == "tf32" else 1.0)
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "tcgen05 fused jet kernel (%s)" % form,
+            "traffic": traffic, "kernel": "tcgen05 fused jet kernel (%s)" % form,
             "peak_kind": "%s bf16_tflops (burst)" % peak_kind}
 
 
@@ -441,7 +475,7 @@ def run_ensemble(args, rank, ws, local):
     e2e_ms = max_over_ranks(e2e_ms, ws)
     flops = sum(i["N"] * flops_per_point(i["widths"], 4) for i in insts)
     peaks, peak_kind = measured_peaks()
-    roof = roofline(form, flops, ms_local, peaks, peak_kind)
+    roof = roofline(form, flops, ms_local, peaks, peak_kind, traffic_for("ensemble_64", form))
     roof["kernel"] = "batched step (graph replay: weight preparation, persistent tcgen05 kernel, reduce + Adam)"
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": W,
            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -487,7 +521,7 @@ def run_ours(args, rank, ws, local):
     C = res["info"]["n_channels"]
     fpp = flops_per_point(spec["widths"], C)
     peaks, peak_kind = measured_peaks()
-    roof = roofline(form, fpp * spec["N"], res["kernel_ms"], peaks, peak_kind)
+    roof = roofline(form, fpp * spec["N"], res["kernel_ms"], peaks, peak_kind, traffic_for(args.workload, form))
     forms = {}
     if not args.no_forms and rank == 0:
         for f in ("fp32", "bf16", "bf16x3", "tf32", "fp64"):
@@ -497,7 +531,8 @@ def run_ours(args, rank, ws, local):
                 r = time_form(spec, f, X, max(3, args.steps // 2), 3, flush, want_kernel=True)
                 forms[f] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernel_ms": r["kernel_ms"],
                             "tile_points": r["info"]["tile_points"], "grid_ctas": r["info"]["grid_ctas"],
-                            "roofline": roofline(f, fpp * spec["N"], r["kernel_ms"], peaks, peak_kind)}
+                            "roofline": roofline(f, fpp * spec["N"], r["kernel_ms"], peaks, peak_kind,
+                                                 traffic_for(args.workload, f))}
             except Exception as e:  # a form this build does not provide
                 forms[f] = {"unavailable": str(e).splitlines()[0][:160]}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
