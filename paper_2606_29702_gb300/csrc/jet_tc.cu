@@ -39,6 +39,9 @@ struct TcPlan {
   int o_w, o_wlo, o_a0, o_a1, o_alo0, o_alo1, o_uo, o_ub, o_xs, o_red, o_part;
   int act_bytes = 0, alo_bytes = 0, r0w = 0, r1w = 0;
   long long scratch_stride = 0;
+  // per-CTA scratch slot: A^1..A^{L-3} copies, then (plans that can run the
+  // weight gradient per tile) the chunk's FP32 weight-gradient accumulator
+  long long wacc_off = -1;
   // workspace
   __nv_bfloat16* Wh = nullptr;   // hidden weights [L-2][w][w]
   __nv_bfloat16* Wl = nullptr;   // output weights [n_out][w]
@@ -501,7 +504,11 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   }
   t->ctas_per_sm = std::min(t->ctas_per_sm, occ);
   t->grid = prop.multiProcessorCount * t->ctas_per_sm;
-  t->scratch_stride = (long long)std::max(0, L - 3) * (t->act_bytes + t->alo_bytes);
+  t->scratch_stride = ((long long)std::max(0, L - 3) * (t->act_bytes + t->alo_bytes) + 15) / 16 * 16;
+  if (!t->single_act) {
+    t->wacc_off = t->scratch_stride;
+    t->scratch_stride += (long long)std::max(0, L - 2) * t->G * t->wu * t->wu * (long long)sizeof(float);
+  }
   // workspace
   const long long nh = (long long)std::max(0, L - 2) * t->w * t->w, nl = (long long)t->G * p->n_out * t->w;
   size_t b_wh = std::max<long long>(nh, 1) * 2, b_wl = nl * 2, b_wlo = t->split3 ? b_wh : 0;
@@ -634,6 +641,7 @@ void fill_tc(const jet_plan_s* p, const TcPlan* t, const void* params, const voi
   I.loss_slices = t->loss_slices;
   I.scratch = t->scratch;
   I.scratch_stride = t->scratch_stride;
+  I.wacc_off = t->wacc_off;
   I.o_w = t->o_w;
   I.o_wlo = t->o_wlo;
   I.o_a0 = t->o_a0;

@@ -26,7 +26,8 @@
 //            epilogue (Zbar^l to shared memory), data gradient
 //            Abar^{l-1} = W^l^T Zbar^l (MN-major A) and weight gradient
 //            Wbar^l = Zbar^l A^{l-1}^T (both operands K-major) by MMA; the
-//            weight gradient is flushed from TMEM into the chunk's FP64 slice.
+//            weight gradient is added from TMEM into the CTA's FP32
+//            accumulator, which reaches the chunk's FP64 slice once per chunk.
 //
 // The layer inputs A^l of a tile are saved to a per-CTA global scratch slot by
 // bulk copies during the forward and read back during the backward, so memory
@@ -117,6 +118,10 @@ struct alignas(64) TcInst {
   double* loss_slices;
   unsigned char* scratch;
   long long scratch_stride;  // bytes per CTA slot
+  // FP32 weight-gradient accumulator of the running chunk, at this byte
+  // offset in the CTA's scratch slot (-1: none; such plans never run the
+  // weight gradient per tile)
+  long long wacc_off;
   // shared-memory carve (bytes from the 1024-aligned base)
   int o_w, o_wlo, o_a0, o_a1, o_alo0, o_alo1, o_uo, o_ub, o_xs, o_red;
   int o_part;  // per-warpgroup partial sums, float [warpgroups][4][256]
@@ -575,78 +580,66 @@ struct TcTile {
     }
   }
 
-  // D[R0] (weight gradient block nb of layer l) -> FP64 slice.  With packed
-  // sub-tiles only the diagonal block of the lane's sub-tile is read: D holds
-  // Zbar A^T over all operand rows, and rows of different sub-tiles belong to
-  // different points.
-  // FP64 adds of a 32-row x 8-column block of the weight gradient (row
-  // row0 + lane, columns k .. k+7, values v) with coalesced addresses: the
-  // warp parks the block in its 1 KB of stg (row-major 32 x 8) and re-reads
-  // it with lanes walking the columns, so every add instruction covers four
-  // contiguous 64-byte runs instead of 32 rows.
-  __device__ void red_block(float* stg, const float* v, int row0, int k, double* gW) const {
-    const int lane = tid & 31;
-    float4* d4 = reinterpret_cast<float4*>(stg + lane * 8);
-    d4[0] = make_float4(v[0], v[1], v[2], v[3]);
-    d4[1] = make_float4(v[4], v[5], v[6], v[7]);
-    __syncwarp();
-    const int col = lane & 7;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int row = t * 4 + (lane >> 3);
-      if (k + col < I.wu) tc::red_add_f64(gW + (long long)(row0 + row) * I.wu + k + col, (double)stg[row * 8 + col]);
-    }
-    __syncwarp();
+  // Weight gradients of a chunk's tiles add up in FP32 in the CTA's scratch
+  // slot and reach the FP64 slice once per chunk (chunk_flush): per-CTA FP32
+  // partials, FP64 across chunks.  Layer l (2..L-1) takes G * wu * wu floats,
+  // laid out [sub][k / 4][u][4], so that the 32 rows of a warp cover 512
+  // contiguous bytes per vector add.  The adds are fire-and-forget FP32
+  // vector reductions; every element belongs to one thread, which adds the
+  // tiles in program order, so the sums are deterministic.
+  __device__ float* wacc(int l) const {
+    return reinterpret_cast<float*>(I.scratch + (long long)blockIdx.x * I.scratch_stride + I.wacc_off) +
+           (long long)(l - 2) * I.G * I.wu * I.wu;
+  }
+  __device__ void wacc_zero() {
+    float4* a = reinterpret_cast<float4*>(wacc(2));
+    const long long n4 = (long long)(I.L - 2) * I.G * I.wu * I.wu / 4;
+    for (long long i = tid; i < n4; i += nthr) a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 
-  // D[R0] (weight gradient block nb of layer l) -> FP64 slice.  With packed
-  // sub-tiles only the diagonal block of the lane's sub-tile is read: D holds
-  // Zbar A^T over all operand rows, and rows of different sub-tiles belong to
-  // different points.  Called by every thread (barriers inside); PART is free
-  // here and serves as each warp's 1 KB staging area.
-  __device__ void flush_wgrad(int l, int nb, int NB, double* g, unsigned char* stage) {
-    double* gW = g + I.off_W[l - 1];
-    float* wst = part + warp * 256;  // this warp's staging block
-    __syncthreads();                 // PART may still be read by the bias flush
-    if (I.G > 1) {
-      // Sub-tiles 1..G-1 park their diagonal blocks in shared memory (the
-      // adjoint buffer, free once the weight-gradient MMA has completed);
-      // sub-tile 0 adds them in FP32 and flushes one FP64 add per weight.
-      // Packed plans have H == 1.
-      float* stg = reinterpret_cast<float*>(stage);
-      const int wu = I.wu, sub = ul / wu, j = ul - sub * wu;
-      if (sub > 0)
-        for (int k0 = wg * 8; k0 < wu; k0 += nwg * 8) {
-          float v[8];
-          tc::tmem_ld8(R0(0) + lane_base() + (uint32_t)(sub * wu + k0), v);
-          tc::tmem_wait_ld();
-          // [block][column][row]: the lanes (rows) of a warp store 32
-          // consecutive floats per column, conflict-free
-          float* dst = stg + ((sub - 1) * wu + k0) * wu + j;
-#pragma unroll
-          for (int i = 0; i < 8; ++i) dst[i * wu] = v[i];
-        }
-      __syncthreads();
-      if (sub == 0)
-        for (int k0 = wg * 8; k0 < wu; k0 += nwg * 8) {
-          float v[8];
-          tc::tmem_ld8(R0(0) + lane_base() + (uint32_t)k0, v);
-          tc::tmem_wait_ld();
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            for (int o = 1; o < I.G; ++o) v[i] += stg[((o - 1) * wu + k0 + i) * wu + j];
-          red_block(wst, v, j - (tid & 31), k0, gW);
-        }
+  // TMEM columns of lane row (8, from taddr) -> accumulator columns k0 .. k0+7
+  // of row u in the [k / 4][u][4] block at acc
+  __device__ void acc8(float* acc, int u, int k0, uint32_t taddr) const {
+    float v[8];
+    tc::tmem_ld8(taddr, v);
+    tc::tmem_wait_ld();
+    const int wu = I.wu;
+    atomicAdd(reinterpret_cast<float4*>(acc + ((long long)(k0 / 4) * wu + u) * 4), make_float4(v[0], v[1], v[2], v[3]));
+    atomicAdd(reinterpret_cast<float4*>(acc + ((long long)(k0 / 4 + 1) * wu + u) * 4), make_float4(v[4], v[5], v[6], v[7]));
+  }
+
+  // D[R0] (weight-gradient columns nb*NB .. of layer l) -> accumulator.  With
+  // packed sub-tiles only the diagonal block of the lane's sub-tile is read:
+  // D holds Zbar A^T over all operand rows, and rows of different sub-tiles
+  // belong to different points.
+  __device__ void acc_wgrad(int l, int nb, int NB) {
+    float* acc = wacc(l);
+    const int wu = I.wu;
+    if (I.G > 1) {  // packed plans have H == 1
+      const int sub = ul / wu, j = ul - sub * wu;
+      float* a = acc + (long long)sub * wu * wu;
+      for (int k0 = wg * 8; k0 < wu; k0 += nwg * 8) acc8(a, j, k0, R0(0) + lane_base() + (uint32_t)(sub * wu + k0));
       return;
     }
     for (int h = 0; h < I.H; ++h) {
       if (h * 128 + q * 32 >= I.w) continue;  // warp-uniform
-      const int row0 = h * 128 + q * 32;     // first weight-gradient row of this warp
-      for (int k0 = wg * 8; k0 < NB; k0 += nwg * 8) {
-        float v[8];
-        tc::tmem_ld8(R0(h) + lane_base() + (uint32_t)k0, v);
-        tc::tmem_wait_ld();
-        red_block(wst, v, row0, nb * NB + k0, gW);
+      for (int k0 = wg * 8; k0 < NB; k0 += nwg * 8) acc8(acc, h * 128 + ul, nb * NB + k0, R0(h) + lane_base() + (uint32_t)k0);
+    }
+  }
+
+  // accumulator (summed over sub-tiles) -> FP64 slice, once per chunk;
+  // consecutive threads take consecutive weights
+  __device__ void chunk_flush(double* g) {
+    const int wu = I.wu;
+    const long long per = (long long)wu * wu;
+    for (int l = 2; l <= I.L - 1; ++l) {
+      const float* acc = wacc(l);
+      double* gW = g + I.off_W[l - 1];
+      for (long long e = tid; e < per; e += nthr) {
+        const int u = (int)(e / wu), k = (int)(e - (long long)u * wu);
+        float s = 0.f;
+        for (int sub = 0; sub < I.G; ++sub) s += __ldcg(acc + ((long long)(sub * (wu / 4) + k / 4) * wu + u) * 4 + (k & 3));
+        tc::red_add_f64(gW + e, (double)s);
       }
     }
   }
@@ -861,7 +854,7 @@ struct TcTile {
       }
       if (!wait(bar_mma, ph_mma, 64)) break;
       tc::tc_fence_after();
-      flush_wgrad(l, 0, NB, g, ACT(zb));
+      acc_wgrad(l, 0, NB);
       for (int nb = 1; nb < nblk; ++nb) {
         sync();
         if (tid == 0) {
@@ -870,7 +863,7 @@ struct TcTile {
         }
         if (!wait(bar_mma, ph_mma, 65)) break;
         tc::tc_fence_after();
-        flush_wgrad(l, nb, NB, g, ACT(zb));
+        acc_wgrad(l, nb, NB);
       }
       sync();
     }
@@ -963,11 +956,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
     double* g = bwd ? I.grad_slices + (I.slice_shared ? 0LL : (long long)chunk * I.n_params) : nullptr;
     if (bwd && !I.slice_shared)
       for (long long i = tid; i < I.n_params; i += nthr) g[i] = 0.0;
+    const bool wacc_on = bwd && !I.wstore && I.L >= 3;  // weight gradients per tile
+    if (wacc_on) T.wacc_zero();
     __syncthreads();
     double loss = 0.0;
     const long long t0 = (long long)chunk * I.tiles_per_chunk;
     const long long t1 = (t0 + I.tiles_per_chunk < I.n_tiles) ? t0 + I.tiles_per_chunk : I.n_tiles;
     for (long long t = t0; t < t1 && !abort_s; ++t) loss += T.tile(t, args.mode, g);
+    // hidden-layer weight gradients of the chunk's tiles -> FP64 slice
+    if (wacc_on && !abort_s) {
+      __threadfence();
+      __syncthreads();
+      T.chunk_flush(g);
+    }
     ph_tma = T.ph_tma;
     ph_mma = T.ph_mma;
     ph_ld = T.ph_ld;

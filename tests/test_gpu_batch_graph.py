@@ -32,8 +32,11 @@ def test_tc_batch_matches_solo_and_oracle():
     b = jet.Batch(plans)
     grads, losses = b.backward(ps, xs)
     torch.cuda.synchronize()
+    # batch and solo runs chunk the tiles differently; a chunk's weight
+    # gradients add up in FP32 (about T * 2^-24 relative for T tiles), the
+    # chunks in FP64
     for i, ins in enumerate(insts):
-        assert rel_l2(grads[i].cpu().numpy(), solo[i][0].cpu().numpy()) < 1e-9
+        assert rel_l2(grads[i].cpu().numpy(), solo[i][0].cpu().numpy()) < 1e-6
         assert abs(float(losses[i]) - float(solo[i][1])) <= 1e-12 * abs(float(solo[i][1]))
         L, _, g_ref = oracle.loss_and_grad(R.by_name(ins["family"], **ins["coefs"]), ins["layers"], ins["X"])
         assert rel_l2(grads[i].cpu().numpy(), wl.pack(g_ref)) < 3e-2
@@ -98,7 +101,7 @@ def test_full_ensemble_one_launch():
     for i in (0, 17, 40, 63):
         g, l, _ = plans[i].backward(ps[i], xs[i])
         torch.cuda.synchronize()
-        assert rel_l2(grads[i].cpu().numpy(), g.cpu().numpy()) < 1e-9
+        assert rel_l2(grads[i].cpu().numpy(), g.cpu().numpy()) < 1e-6  # FP32 chunk sums, as above
     assert torch.isfinite(losses).all()
 
 

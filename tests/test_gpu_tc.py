@@ -255,7 +255,8 @@ def test_tc_packed_subtiles_any_tile(width, tiles):
 @pytest.mark.parametrize("widths,tile,ctas", [([2, 32, 32, 32, 1], 32, 1), ([2, 64, 64, 64, 1], 16, 1),
                                               ([2, 64, 64, 64, 1], 32, 2), ([2, 128, 128, 1], 8, 1)])
 def test_tc_backward_bitwise_repeatable(widths, tile, ctas):
-    """Per-chunk FP64 gradient slices make repeated calls bitwise identical;
+    """Fixed-order sums (each weight's FP32 chunk accumulator belongs to one
+    thread, each chunk to one FP64 slice) make repeated calls bitwise identical;
     a cross-warpgroup race on the partial-sum area would show up here as
     run-to-run differences (small tiles, all warpgroups active)."""
     from paper_2606_29702_gb300 import jet, specs
