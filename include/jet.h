@@ -129,6 +129,12 @@ typedef struct {
   size_t workspace_bytes;  /* device memory the plan owns */
   int32_t ctas_per_sm;     /* CTAs of the fused kernel resident per SM */
   int32_t cta_threads;     /* threads per CTA of the fused kernel */
+  int32_t wgrad_chunk_fp32; /* 1: hidden-layer weight gradients computed per
+                               tile add up in an FP32 accumulator per CTA and
+                               reach the FP64 chunk sums once per chunk; 0:
+                               they are added into the FP64 chunk sums per
+                               tile (FP64 forms; FP32 plans whose FP64 chunk
+                               sums fit in L2) */
 } jet_plan_info;
 
 /*

@@ -319,11 +319,18 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
   long long jet_elems = 0;  // hidden z-jets of one tile
   for (int l = 1; l < n_layers; ++l) jet_elems += (long long)p->C * p->P * widths[l];
   if (!p->tc) {
-    p->scratch_stride = jet_elems;
+    // FP32 forms whose per-chunk FP64 slices would not stay in L2 add the
+    // hidden-layer weight gradients of a chunk in an FP32 accumulator and
+    // flush once per chunk; otherwise per-tile FP64 adds into L2-resident
+    // slices are the cheaper of the two
+    const bool slices_fit = (double)p->grid * p->n_params * sizeof(double) <= kSimtSliceL2Bytes;
+    const long long wacc = slices_fit ? 0 : simt_wacc_elems(widths, n_layers, p->fp64);
+    p->scratch_stride = jet_elems + wacc;
+    p->wacc_off = wacc ? jet_elems : -1;
     size_t b_wt = (size_t)weight_ws_elems(p->n_params) * p->elem;
     size_t b_gs = (size_t)p->grid * p->n_params * sizeof(double);
     size_t b_ls = (size_t)p->grid * sizeof(double);
-    size_t b_sc = (size_t)p->grid * jet_elems * p->elem;
+    size_t b_sc = (size_t)p->grid * p->scratch_stride * p->elem;
     e = cudaMalloc(&p->Wt, b_wt);
     if (e == cudaSuccess) e = cudaMalloc((void**)&p->grad_slices, b_gs);
     if (e == cudaSuccess) e = cudaMalloc((void**)&p->loss_slices, b_ls);
@@ -374,6 +381,7 @@ jet_status jet_plan_get_info(jet_plan_t p, jet_plan_info* info) {
   info->workspace_bytes = p->tc ? tc_workspace_bytes(p->tcp) : p->ws_bytes;
   info->ctas_per_sm = p->tc ? tc_ctas_per_sm(p->tcp) : p->ctas_per_sm;
   info->cta_threads = p->tc ? tc_threads(p->tcp) : kSimtThreads;
+  info->wgrad_chunk_fp32 = p->tc ? tc_wgrad_chunk_fp32(p->tcp) : (p->wacc_off >= 0 ? 1 : 0);
   return JET_OK;
 }
 
@@ -450,6 +458,7 @@ void fill_instance(const jet_plan_s* p, const void* params, const void* X, long 
   I.loss_slices = p->loss_slices;
   I.store = nullptr;
   I.store_tile_stride = p->store_tile_stride;
+  I.wacc_off = p->wacc_off;
 }
 
 jet_status check_call(const jet_plan_s* p, const void* params, const void* X, long long N, const void* source) {

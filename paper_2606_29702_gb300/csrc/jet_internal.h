@@ -62,6 +62,9 @@ struct DevInstance {
   // [w][C * P] (as the shared-memory rows); null if not stored
   void* store;
   long long store_tile_stride;  // elements per tile
+  // FP32 forms: element offset, in a CTA's scratch slot, of the chunk's FP32
+  // weight-gradient accumulator (simt_wacc_elems); -1: FP64 adds per tile
+  long long wacc_off;
 };
 
 // Per-launch arguments of the fused SIMT kernel.
@@ -84,6 +87,18 @@ constexpr int kSimtThreads = 256;
 inline int simt_point_stride(int C, int P) {
   const int lanes = P < 32 ? P : 32;
   return (C & -C) * lanes <= 32 ? C : (C | 1);
+}
+// share of L2 the per-chunk FP64 gradient slices may take before the kernels
+// accumulate a chunk's weight gradients in FP32 instead of adding per tile
+constexpr double kSimtSliceL2Bytes = 48.0 * 1024 * 1024;
+// FP32 forms: elements of the per-CTA weight-gradient accumulator that
+// follows a tile's z-jets in the CTA's scratch slot, one float per weight of
+// every hidden-to-hidden layer W^l (l = 2 .. L-1, [w_l][w_{l-1}])
+inline long long simt_wacc_elems(const int* widths, int L, bool fp64) {
+  if (fp64) return 0;
+  long long e = 0;
+  for (int l = 2; l <= L - 1; ++l) e += (long long)widths[l] * widths[l - 1];
+  return e;
 }
 // elements of the SIMT weight workspace: transposed copy, then aligned copy
 __host__ __device__ inline long long weight_copy_offset(long long n_params) { return (n_params + 3) & ~3LL; }

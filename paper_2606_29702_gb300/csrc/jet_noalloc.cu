@@ -243,6 +243,7 @@ extern "C" jet_status jet_backward_params_noalloc(const jet_residual_spec* spec,
   if (scratch_bytes_used) *scratch_bytes_used = used;
   I.chunk_base = 0;
   I.store = nullptr;
+  I.wacc_off = -1;  // its few chunks' FP64 slices stay in L2: FP64 adds per tile
 
   cudaStream_t s = (cudaStream_t)stream;
   // every buffer below is fully written before it is read: the transpose

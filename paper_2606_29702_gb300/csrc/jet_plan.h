@@ -35,6 +35,7 @@ struct jet_plan_s {
   double* loss_slices = nullptr;
   void* scratch = nullptr;
   long long scratch_stride = 0;
+  long long wacc_off = -1;  // FP32 weight-gradient accumulator in a scratch slot (elements)
   void* store = nullptr;
   long long store_max_points = 0;
   long long store_tile_stride = 0;

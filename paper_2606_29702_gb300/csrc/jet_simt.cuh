@@ -101,6 +101,12 @@ __device__ __forceinline__ void vstore(T* p, const T* in) {
   *reinterpret_cast<V*>(p) = v;
 }
 
+// p[0..3] += (a, b, c, d) in global memory as one fire-and-forget FP32
+// vector reduction (16-byte aligned; no value comes back, so nothing waits)
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
 struct SimtSmem {
   int P, pitch, wmax, C, nout, d;
   __device__ size_t buf_elems() const { return (size_t)wmax * pitch; }
@@ -125,6 +131,11 @@ struct SimtTile {
   const T* params;
   const T* Wt;  // transposed weights [in][out] per layer
   const T* Wc;  // aligned copy of the packed parameters
+  // FP32 forms: the chunk's hidden-layer weight gradients add up in FP32 in
+  // this CTA's scratch slot (fire-and-forget vector reductions; every element
+  // belongs to one thread, which adds the tiles in program order) and reach
+  // the FP64 slice once per chunk.  Null: FP64 adds per tile.
+  float* wacc_base = nullptr;
 
   __device__ SimtTile(const DevInstance& I_, const SimtArgs& A_, unsigned char* smem) : I(I_), A(A_) {
     P = I.P;
@@ -146,6 +157,42 @@ struct SimtTile {
     params = reinterpret_cast<const T*>(I.params);
     Wt = reinterpret_cast<const T*>(I.Wt);
     Wc = Wt + weight_copy_offset(I.n_params);
+    if (sizeof(T) == 4 && I.wacc_off >= 0)
+      wacc_base = reinterpret_cast<float*>(A.scratch) + (long long)blockIdx.x * A.scratch_stride + I.wacc_off;
+  }
+
+  // accumulator of W^l (l = 2..L-1): [item][4][4] per thread item of wgrad
+  __device__ float* wacc(int l) const {
+    long long off = 0;
+    for (int k = 2; k < l; ++k) off += (long long)I.widths[k] * I.widths[k - 1];
+    return wacc_base + off;
+  }
+  __device__ void wacc_zero() {
+    float4* a = reinterpret_cast<float4*>(wacc_base);
+    const long long n4 = (wacc(I.L) - wacc_base) / 4;
+    for (long long i = threadIdx.x; i < n4; i += NT) a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  // accumulator -> FP64 slice (consecutive threads read consecutive floats;
+  // eight loads in flight before their adds)
+  __device__ void wacc_flush(double* g) {
+    for (int l = 2; l <= I.L - 1; ++l) {
+      const int wo = I.widths[l], wi = I.widths[l - 1], nkb = wi / 4, n = wo * wi;
+      const float* a = wacc(l);
+      double* gW = g + I.off_W[l - 1];
+      for (int e0 = threadIdx.x; e0 < n; e0 += 8 * NT) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = e0 + j * NT < n ? __ldcg(a + e0 + j * NT) : 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int e = e0 + j * NT;
+          if (e >= n) break;
+          const int it = e >> 4, r = (e >> 2) & 3, s = e & 3;
+          const int kb = it % nkb, ub = it / nkb;
+          atomicAdd(gW + (ub * 4 + r) * wi + kb + s * nkb, (double)v[j]);
+        }
+      }
+    }
   }
 
   __device__ const T* W(int l) const { return params + I.off_W[l - 1]; }   // l = 1..L
@@ -533,8 +580,16 @@ struct SimtTile {
               for (int j = 0; j < TP; ++j) acc[r][s] = fma(zv[r][j], av[s][j], acc[r][s]);
         }
       }
-      // fire-and-forget FP64 adds: every slice element belongs to one thread,
-      // which adds the tiles in order, so the sums stay deterministic
+      // fire-and-forget adds: every element belongs to one thread, which adds
+      // the tiles in order, so the sums stay deterministic
+      if constexpr (sizeof(T) == 4) {
+        if (wacc_base) {
+          float* a = wacc(l) + (long long)it * 16;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) red_add_v4(a + 4 * r, acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+          continue;
+        }
+      }
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -677,6 +732,8 @@ __global__ void __launch_bounds__(kSimtThreads) simt_kernel(const __grid_constan
     double* g = bwd ? I.grad_slices + (long long)chunk * I.n_params : nullptr;
     if (bwd)
       for (long long i = threadIdx.x; i < I.n_params; i += kSimtThreads) g[i] = 0.0;
+    const bool wacc_on = bwd && S.wacc_base != nullptr;
+    if (wacc_on) S.wacc_zero();
     __syncthreads();
     double loss = 0.0;
     const long long t0 = (long long)chunk * I.tiles_per_chunk;
@@ -684,6 +741,11 @@ __global__ void __launch_bounds__(kSimtThreads) simt_kernel(const __grid_constan
     for (long long t = t0; t < t1; ++t) {
       loss += S.tile(t, g);
       __syncthreads();
+    }
+    if (wacc_on) {
+      __threadfence();
+      __syncthreads();
+      S.wacc_flush(g);
     }
     // block reduction of the loss partial (fixed order)
     for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);

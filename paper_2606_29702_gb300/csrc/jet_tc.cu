@@ -581,6 +581,7 @@ int tc_tile_points(const TcPlan* t) { return t ? t->P : 0; }
 int tc_grid(const TcPlan* t) { return t ? t->grid : 0; }
 int tc_ctas_per_sm(const TcPlan* t) { return t ? t->ctas_per_sm : 0; }
 int tc_threads(const TcPlan* t) { return t ? t->nthreads : 0; }
+int tc_wgrad_chunk_fp32(const TcPlan* t) { return t && t->wacc_off >= 0 ? 1 : 0; }
 size_t tc_workspace_bytes(const TcPlan* t) { return t ? t->ws_bytes : 0; }
 
 namespace {

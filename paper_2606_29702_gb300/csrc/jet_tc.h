@@ -21,6 +21,7 @@ int tc_tile_points(const jet::TcPlan* t);
 int tc_grid(const jet::TcPlan* t);
 int tc_ctas_per_sm(const jet::TcPlan* t);
 int tc_threads(const jet::TcPlan* t);
+int tc_wgrad_chunk_fp32(const jet::TcPlan* t);  // per-tile weight gradients use the FP32 chunk accumulator
 size_t tc_workspace_bytes(const jet::TcPlan* t);
 jet_status tc_forward(jet_plan_s* p, jet::TcPlan* t, const void* params, const void* X, long long N,
                       const void* source, void* r_out, double* loss_out, cudaStream_t s);

@@ -604,8 +604,8 @@ struct TcTile {
     tc::tmem_ld8(taddr, v);
     tc::tmem_wait_ld();
     const int wu = I.wu;
-    atomicAdd(reinterpret_cast<float4*>(acc + ((long long)(k0 / 4) * wu + u) * 4), make_float4(v[0], v[1], v[2], v[3]));
-    atomicAdd(reinterpret_cast<float4*>(acc + ((long long)(k0 / 4 + 1) * wu + u) * 4), make_float4(v[4], v[5], v[6], v[7]));
+    red_add_v4(acc + ((long long)(k0 / 4) * wu + u) * 4, v[0], v[1], v[2], v[3]);
+    red_add_v4(acc + ((long long)(k0 / 4 + 1) * wu + u) * 4, v[4], v[5], v[6], v[7]);
   }
 
   // D[R0] (weight-gradient columns nb*NB .. of layer l) -> accumulator.  With
@@ -628,18 +628,28 @@ struct TcTile {
   }
 
   // accumulator (summed over sub-tiles) -> FP64 slice, once per chunk;
-  // consecutive threads take consecutive weights
+  // consecutive threads take consecutive weights, eight per batch with their
+  // loads in flight before the adds
   __device__ void chunk_flush(double* g) {
-    const int wu = I.wu;
-    const long long per = (long long)wu * wu;
+    const int wu = I.wu, per = wu * wu;
     for (int l = 2; l <= I.L - 1; ++l) {
       const float* acc = wacc(l);
       double* gW = g + I.off_W[l - 1];
-      for (long long e = tid; e < per; e += nthr) {
-        const int u = (int)(e / wu), k = (int)(e - (long long)u * wu);
-        float s = 0.f;
-        for (int sub = 0; sub < I.G; ++sub) s += __ldcg(acc + ((long long)(sub * (wu / 4) + k / 4) * wu + u) * 4 + (k & 3));
-        tc::red_add_f64(gW + e, (double)s);
+      for (int e0 = tid; e0 < per; e0 += 8 * nthr) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int e = e0 + j * nthr;
+          v[j] = 0.f;
+          if (e < per) {
+            const int u = e / wu, k = e - u * wu;
+            for (int sub = 0; sub < I.G; ++sub)
+              v[j] += __ldcg(acc + ((long long)(sub * (wu / 4) + k / 4) * wu + u) * 4 + (k & 3));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (e0 + j * nthr < per) tc::red_add_f64(gW + e0 + j * nthr, (double)v[j]);
       }
     }
   }

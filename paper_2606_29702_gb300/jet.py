@@ -48,7 +48,8 @@ class JetPlanInfo(ctypes.Structure):
                 ("class_name", ctypes.c_char * 32), ("n_params", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("store_mode", ctypes.c_int32), ("store_max_points", ctypes.c_int64),
                 ("tile_points", ctypes.c_int32), ("grid_ctas", ctypes.c_int32), ("workspace_bytes", ctypes.c_size_t),
-                ("ctas_per_sm", ctypes.c_int32), ("cta_threads", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
+                ("wgrad_chunk_fp32", ctypes.c_int32)]
 
 
 EXPORTS = ["jet_plan_create", "jet_plan_get_info", "jet_forward_residual", "jet_backward_params", "jet_train_step",

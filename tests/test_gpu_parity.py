@@ -65,6 +65,22 @@ def test_simt_matches_oracle(name, prec, N, widths):
     np.testing.assert_array_equal(r_b, r)
 
 
+@pytest.mark.parametrize("name,N,chunk_fp32", [("ks_2x64x5", 999, 0), ("ns_psi_3x128x6", 301, 1)])
+def test_simt_fp32_weight_gradient_paths(name, N, chunk_fp32):
+    """FP32 plans whose per-chunk FP64 gradient slices fit in L2 add weight
+    gradients into them per tile; wider ones accumulate a chunk's tiles in
+    FP32 first.  Either way each sum has one owner thread and a fixed order:
+    repeated calls are bitwise identical, and both match the oracle."""
+    spec, X, layers, src = case(name, N)
+    L, r_ref, g_ref = reference(spec, X, layers)
+    r, loss, g, _, _, plan = _run(spec, X, layers, src, "fp32")
+    assert plan.info()["wgrad_chunk_fp32"] == chunk_fp32
+    assert rel_l2(g, g_ref) <= TOL["fp32"][1]
+    for _ in range(2):
+        _, _, g2, _, _, _ = _run(spec, X, layers, src, "fp32", plan=plan)
+        np.testing.assert_array_equal(g2, g)
+
+
 @pytest.mark.parametrize("N", [1, 2, 7, 47, 48, 49, 100])
 def test_ragged_tails_fp64(N):
     spec, X, layers, src = case("burgers_2x20x4", N, seed_shift=N)

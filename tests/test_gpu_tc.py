@@ -281,6 +281,9 @@ def test_tc_single_buffer_store_plan_limits():
     widths = [3, 256, 256, 256, 256, 1]
     sp = specs.helmholtz(4 * math.pi)
     plan = jet.Plan(sp, widths, "bf16", store=True, mem_budget=1 << 20)
+    # the weight gradient of such a plan is always the separate GEMM
+    assert plan.info()["wgrad_chunk_fp32"] == 0
+    assert jet.Plan(sp, widths, "bf16").info()["wgrad_chunk_fp32"] == 1
     assert plan.info()["tile_points"] == 16
     X = wl.points([(-1, 1)] * 3, 200, 1)
     p = _dev(wl.pack(wl.xavier_layers(widths, 2)))
