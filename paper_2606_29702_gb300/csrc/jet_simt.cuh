@@ -119,6 +119,9 @@ struct SimtTile {
   static constexpr int TP = Vec<T>::N;
   static constexpr int NT = kSimtThreads;
   static constexpr int RU = TP;  // consecutive units per thread
+  // k-steps of the jet GEMMs unrolled together (loads in flight): wide
+  // channel sets gain from four, KS-sized ones lose (measured)
+  static constexpr int UK = C >= 7 ? 4 : 2;
 
   const DevInstance& I;
   const SimtArgs& A;
@@ -293,7 +296,7 @@ struct SimtTile {
         for (int c = 0; c < C; ++c) acc[r][c] = T(0);
       const T* ap = in + n * S;  // row k of A^{l-1}, this point's channels
       const T* wp = Wtl + u0;    // row k of W^l^T, this thread's units
-#pragma unroll 2
+#pragma unroll(UK)
       for (int k = 0; k < wi; ++k, ap += pitch, wp += wo) {
         T wv[RU], av[C];
         vldg<T>(wp, wv);
@@ -618,7 +621,7 @@ struct SimtTile {
         for (int c = 0; c < C; ++c) acc[i][c] = T(0);
       const T* zp = zbar + n * S;  // row u of Zbar^l, this point's channels
       const T* wp = Wl + k0;       // row u of W^l, this thread's input units
-#pragma unroll 2
+#pragma unroll(UK)
       for (int u = 0; u < wo; ++u, zp += pitch, wp += wi) {
         T wv[RU], zv[C];
         vldg<T>(wp, wv);
