@@ -422,40 +422,86 @@ struct TcTile {
     }
   }
 
+  // Residual r_c = sum of the monomials - source, the loss partial and (bwd)
+  // ub = dL/du.  Three parallel passes over (point, monomial) products, per
+  // point sums and per (point, output channel) adjoints, which keep every
+  // sum's operands and order those of a per-point loop over the monomials;
+  // the products and scaled residuals live in the partial-sum area (free
+  // here).  Spec-sized work that does not fit takes the per-point loop.
   __device__ double residual(long long n0, int nvalid, bool bwd) {
     float* uo = UO();
     float* ub = UB();
-    const int P = I.P;
+    const int P = I.P, nt = I.n_terms, nslot = I.n_out * C;
+    const float two_over_n = (float)(2.0 * I.inv_N);
     double loss = 0.0;
-    if (bwd)
-      for (int i = tid; i < I.n_out * C * P; i += nthr) ub[i] = 0.f;
+    if ((nt + I.n_res) * P > nwg * 4 * 256) {
+      if (bwd)
+        for (int i = tid; i < nslot * P; i += nthr) ub[i] = 0.f;
+      __syncthreads();
+      for (int n = tid; n < nvalid; n += nthr) {
+        float r[kMaxRes];
+        for (int c = 0; c < I.n_res; ++c) r[c] = I.source ? -I.source[(n0 + n) * I.n_res + c] : 0.f;
+        for (int m = 0; m < nt; ++m) {
+          const DevTerm& tm = I.terms[m];
+          float prod = (float)tm.coef;
+          for (int f = 0; f < tm.nfac; ++f) prod *= uo[tm.fac[f] * P + n];
+          r[tm.comp] += prod;
+        }
+        for (int c = 0; c < I.n_res; ++c) {
+          if (I.r_out) I.r_out[(n0 + n) * I.n_res + c] = r[c];
+          loss += (double)r[c] * (double)r[c];
+        }
+        if (bwd)
+          for (int m = 0; m < nt; ++m) {
+            const DevTerm& tm = I.terms[m];
+            const float gg = two_over_n * r[tm.comp] * (float)tm.coef;
+            for (int f = 0; f < tm.nfac; ++f) {
+              float prod = gg;
+              for (int q = 0; q < tm.nfac; ++q)
+                if (q != f) prod *= uo[tm.fac[q] * P + n];
+              ub[tm.fac[f] * P + n] += prod;
+            }
+          }
+      }
+      return loss;
+    }
+    float* prodm = part;            // [n_terms][P] monomial values
+    float* rg = part + nt * P;      // [n_res][P] 2 r / N
+    for (int i = tid; i < nt * nvalid; i += nthr) {
+      const int m = i / nvalid, n = i - m * nvalid;
+      const DevTerm& tm = I.terms[m];
+      float prod = (float)tm.coef;
+      for (int f = 0; f < tm.nfac; ++f) prod *= uo[tm.fac[f] * P + n];
+      prodm[m * P + n] = prod;
+    }
     __syncthreads();
     for (int n = tid; n < nvalid; n += nthr) {
       float r[kMaxRes];
       for (int c = 0; c < I.n_res; ++c) r[c] = I.source ? -I.source[(n0 + n) * I.n_res + c] : 0.f;
-      for (int m = 0; m < I.n_terms; ++m) {
-        const DevTerm& tm = I.terms[m];
-        float prod = (float)tm.coef;
-        for (int f = 0; f < tm.nfac; ++f) prod *= uo[tm.fac[f] * P + n];
-        r[tm.comp] += prod;
-      }
+      for (int m = 0; m < nt; ++m) r[I.terms[m].comp] += prodm[m * P + n];
       for (int c = 0; c < I.n_res; ++c) {
         if (I.r_out) I.r_out[(n0 + n) * I.n_res + c] = r[c];
         loss += (double)r[c] * (double)r[c];
+        rg[c * P + n] = two_over_n * r[c];
       }
-      if (bwd) {
-        const float two_over_n = (float)(2.0 * I.inv_N);
-        for (int m = 0; m < I.n_terms; ++m) {
+    }
+    if (!bwd) return loss;
+    __syncthreads();
+    for (int i = tid; i < nslot * P; i += nthr) {
+      const int k = i / P, n = i - k * P;
+      float acc = 0.f;
+      if (n < nvalid)
+        for (int m = 0; m < nt; ++m) {
           const DevTerm& tm = I.terms[m];
-          const float gg = two_over_n * r[tm.comp] * (float)tm.coef;
           for (int f = 0; f < tm.nfac; ++f) {
-            float prod = gg;
+            if (tm.fac[f] != k) continue;
+            float prod = rg[tm.comp * P + n] * (float)tm.coef;
             for (int q = 0; q < tm.nfac; ++q)
               if (q != f) prod *= uo[tm.fac[q] * P + n];
-            ub[tm.fac[f] * P + n] += prod;
+            acc += prod;
           }
         }
-      }
+      ub[i] = acc;
     }
     return loss;
   }
