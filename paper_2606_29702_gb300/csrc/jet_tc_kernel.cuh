@@ -321,12 +321,14 @@ struct TcTile {
   // ------------------------------------------------------------ forward pieces
   __device__ void layer1_fwd(int out_buf) {
     const float* Pm = I.params;
-    const int Pc = I.Pc, d = I.d;
+    const int Pc = I.Pc;
+    constexpr int d = Cls::D;  // the plan's input dimension
     for (int h = 0; h < I.H; ++h) {
       const int r = h * 128 + ul;  // operand row
       if (r >= I.w) continue;
       const int sub = r / I.wu, u = r - sub * I.wu;
-      float w1[3] = {0.f, 0.f, 0.f};
+      float w1[d];
+#pragma unroll
       for (int i = 0; i < d; ++i) w1[i] = Pm[I.off_W[0] + u * d + i];
       const float b1 = Pm[I.off_b[0] + u];
       const float* xs = XS() + sub * Pc * d;
@@ -338,6 +340,7 @@ struct TcTile {
 #pragma unroll
           for (int c = 0; c < C; ++c) z[c] = f2(0.f);
           float v0 = b1, v1 = b1;
+#pragma unroll
           for (int i = 0; i < d; ++i) {
             v0 = fmaf(w1[i], xs[(g + j) * d + i], v0);
             v1 = fmaf(w1[i], xs[(g + j + 1) * d + i], v1);
@@ -533,12 +536,14 @@ struct TcTile {
     }
   }
 
-  // sum of slot k of PART over warpgroups and sub-tiles for true unit u
+  // sum of slot k of PART over warpgroups and sub-tiles for true unit u, in
+  // FP32 and a fixed order (at most 16 FP32 partials of one tile; the FP64
+  // adds across tiles follow)
   __device__ double part_sum(int k, int u) const {
-    double s = 0.0;
+    float s = 0.f;
     for (int sub = 0; sub < I.G; ++sub)
-      for (int w2 = 0; w2 < nwg; ++w2) s += (double)PART(w2, k, sub * I.wu + u);
-    return s;
+      for (int w2 = 0; w2 < nwg; ++w2) s += PART(w2, k, sub * I.wu + u);
+    return (double)s;
   }
 
   __device__ void out_grads_flush(double* g) {
@@ -704,19 +709,23 @@ struct TcTile {
   __device__ void layer1_bwd(bool abar_from_ub) {
     const float* Pm = I.params;
     const float* ub = UB();
-    const int P = I.P, Pc = I.Pc, d = I.d;
+    const int P = I.P, Pc = I.Pc;
+    constexpr int d = Cls::D;  // the plan's input dimension
     for (int h = 0; h < I.H; ++h) {
       const int r = h * 128 + ul;
       if (h * 128 + q * 32 >= I.w) continue;
       const int sub = r / I.wu, u = r - sub * I.wu;
-      float w1[3] = {0.f, 0.f, 0.f};
+      float w1[d];
+#pragma unroll
       for (int i = 0; i < d; ++i) w1[i] = Pm[I.off_W[0] + u * d + i];
       const float b1 = Pm[I.off_b[0] + u];
       float wl[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
       if (abar_from_ub)
         for (int o = 0; o < I.n_out; ++o) wl[o] = Pm[I.off_W[I.L - 1] + (long long)o * I.wu + u];
       const float* xs = XS() + sub * Pc * d;
-      float gw[3] = {0.f, 0.f, 0.f}, gb = 0.f;
+      float gw[d], gb = 0.f;
+#pragma unroll
+      for (int i = 0; i < d; ++i) gw[i] = 0.f;
       for (int g = wg * PPB; g < Pc; g += nwg * PPB) {
         float abv[C][PPB];
         if (!abar_from_ub) {
@@ -742,6 +751,7 @@ struct TcTile {
             ab[c] = f2(abv[c][j], abv[c][j + 1]);
           }
           float v0 = b1, v1 = b1;
+#pragma unroll
           for (int i = 0; i < d; ++i) {
             v0 = fmaf(w1[i], xs[(g + j) * d + i], v0);
             v1 = fmaf(w1[i], xs[(g + j + 1) * d + i], v1);
@@ -756,6 +766,7 @@ struct TcTile {
           Cls::adjoint(z, p, ab, zb);
           gb += zb[0].v.x;
           gb += zb[0].v.y;
+#pragma unroll
           for (int i = 0; i < d; ++i) {
             gw[i] = fmaf(zb[0].v.x, xs[(g + j) * d + i], gw[i]);
             gw[i] = fmaf(zb[0].v.y, xs[(g + j + 1) * d + i], gw[i]);
@@ -770,13 +781,14 @@ struct TcTile {
           }
         }
       }
-      for (int i = 0; i < 3; ++i) PART(wg, i, r) = gw[i];
+#pragma unroll
+      for (int i = 0; i < d; ++i) PART(wg, i, r) = gw[i];
       PART(wg, 3, r) = gb;
     }
   }
 
   __device__ void layer1_flush(double* g) {
-    for (int i = 0; i < I.d; ++i) part_flush(i, g + I.off_W[0] + i, I.d);
+    for (int i = 0; i < Cls::D; ++i) part_flush(i, g + I.off_W[0] + i, Cls::D);
     part_flush(3, g + I.off_b[0], 1);
   }
 
