@@ -873,16 +873,18 @@ struct TcTile {
     out_grads_flush(g);
     __syncthreads();  // PART is rewritten by the first adjoint epilogue
     const int zb = cur, ain = cur ^ 1;
+    // thread 0: A^{l-1} and W^l for the recompute of layer l, requested as
+    // soon as the MMAs of layer l+1 have released both buffers
+    auto request_reload = [&](int l) {
+      tc::bulk_wait0();
+      tc::mbar_arrive_expect_tx(bar_ld, (uint32_t)(I.act_bytes + (I.split3 ? I.alo_bytes : 0)));
+      tc::bulk_g2s(ACT(ain), slot(l - 1), (uint32_t)I.act_bytes, bar_ld);
+      if (I.split3) tc::bulk_g2s(ALO(ain), slot(l - 1) + I.act_bytes, (uint32_t)I.alo_bytes, bar_ld);
+      load_hidden_w(l);
+    };
     for (int l = L - 1; l >= 2; --l) {
       if (l < L - 1) {
-        // reload A^{l-1} and W^l, recompute z^l = W^l A^{l-1} into R0
-        if (tid == 0) {
-          tc::bulk_wait0();
-          tc::mbar_arrive_expect_tx(bar_ld, (uint32_t)(I.act_bytes + (I.split3 ? I.alo_bytes : 0)));
-          tc::bulk_g2s(ACT(ain), slot(l - 1), (uint32_t)I.act_bytes, bar_ld);
-          if (I.split3) tc::bulk_g2s(ALO(ain), slot(l - 1) + I.act_bytes, (uint32_t)I.alo_bytes, bar_ld);
-          load_hidden_w(l);
-        }
+        // recompute z^l = W^l A^{l-1} into R0
         if (!wait(bar_ld, ph_ld, 60)) break;
         if (!wait(bar_tma, ph_tma, 61)) break;
         if (tid == 0) {
@@ -898,7 +900,6 @@ struct TcTile {
       adjoint_epilogue(l, zb, l == L - 1);
       tc::fence_proxy_async_smem();
       sync();
-      part_flush(0, g + I.off_b[l - 1], 1);  // bias gradient of layer l
       if (store) {
         // Zbar^l goes to the store; the weight gradient is a separate GEMM
         if (tid == 0) {
@@ -907,9 +908,13 @@ struct TcTile {
           mma_dgrad(zb);
           tc::mma_commit(bar_mma);
         }
+        part_flush(0, g + I.off_b[l - 1], 1);  // bias gradient of layer l, during the MMA
         if (!wait(bar_mma, ph_mma, 66)) break;
         tc::tc_fence_after();
-        if (tid == 0) tc::bulk_wait_read0();  // ACT(zb) is rewritten by the next adjoint
+        if (tid == 0) {
+          tc::bulk_wait_read0();  // ACT(zb) is rewritten by the reload or the next adjoint
+          if (l > 2) request_reload(l - 1);
+        }
         sync();
         continue;
       }
@@ -920,8 +925,10 @@ struct TcTile {
         mma_wgrad(zb, ain, 0, NB);
         tc::mma_commit(bar_mma);
       }
+      part_flush(0, g + I.off_b[l - 1], 1);  // bias gradient of layer l, during the MMAs
       if (!wait(bar_mma, ph_mma, 64)) break;
       tc::tc_fence_after();
+      if (tid == 0 && nblk == 1 && l > 2) request_reload(l - 1);
       acc_wgrad(l, 0, NB);
       for (int nb = 1; nb < nblk; ++nb) {
         sync();
@@ -931,6 +938,7 @@ struct TcTile {
         }
         if (!wait(bar_mma, ph_mma, 65)) break;
         tc::tc_fence_after();
+        if (tid == 0 && nb == nblk - 1 && l > 2) request_reload(l - 1);
         acc_wgrad(l, nb, NB);
       }
       sync();
