@@ -175,13 +175,13 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
 # null.  The Helmholtz entry was captured at N = 32768 and scaled by the point
 # count (its traffic is the per-tile store, proportional to N).
 TRAFFIC = {
-    ("ks_2x64x5", "fp32"): (9756928 + 807334144, "12333ac7561a7e7b"),
-    ("ks_2x64x5", "bf16"): (885504 + 9101056, "12333ac7561a7e7b"),
-    ("ks_2x64x5", "bf16x3"): (1018880 + 15339264, "12333ac7561a7e7b"),
-    ("ks_2x64x5", "fp64"): (5640448 + 520318720, "12333ac7561a7e7b"),
-    ("ns_psi_3x128x6", "bf16"): (4340224 + 41560320, "12333ac7561a7e7b"),
-    ("helmholtz_3x256x8", "bf16"): ((314044928 + 1863854848) * 32, "12333ac7561a7e7b"),
-    ("ensemble_64", "bf16"): (2783134976 + 8973665024, "12333ac7561a7e7b"),
+    ("ks_2x64x5", "fp32"): (12168704 + 814621184, "f5c4a516bedbe0f9"),
+    ("ks_2x64x5", "bf16"): (872960 + 18830848, "f5c4a516bedbe0f9"),
+    ("ks_2x64x5", "bf16x3"): (1010688 + 30788352, "f5c4a516bedbe0f9"),
+    ("ks_2x64x5", "fp64"): (9929984 + 518699776, "f5c4a516bedbe0f9"),
+    ("ns_psi_3x128x6", "bf16"): (101470464 + 8315597824, "f5c4a516bedbe0f9"),
+    ("helmholtz_3x256x8", "bf16"): ((316041216 + 1837526016) * 32, "f5c4a516bedbe0f9"),
+    ("ensemble_64", "bf16"): (780659456 + 5521017856, "f5c4a516bedbe0f9"),
 }
 
 

@@ -170,14 +170,14 @@ struct SimtTile {
     for (int k = 2; k < l; ++k) off += (long long)I.widths[k] * I.widths[k - 1];
     return wacc_base + off;
   }
-  __device__ void wacc_zero() {
+  __device__ __noinline__ void wacc_zero() {
     float4* a = reinterpret_cast<float4*>(wacc_base);
     const long long n4 = (wacc(I.L) - wacc_base) / 4;
     for (long long i = threadIdx.x; i < n4; i += NT) a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   // accumulator -> FP64 slice (consecutive threads read consecutive floats;
   // eight loads in flight before their adds)
-  __device__ void wacc_flush(double* g) {
+  __device__ __noinline__ void wacc_flush(double* g) {
     for (int l = 2; l <= I.L - 1; ++l) {
       const int wo = I.widths[l], wi = I.widths[l - 1], nkb = wi / 4, n = wo * wi;
       const float* a = wacc(l);
@@ -717,8 +717,10 @@ struct SimtTile {
   }
 };
 
+constexpr int kWaccTiles = 64;  // tiles per FP32 weight-gradient run (FP32 forms)
+
 template <class Cls, class T>
-__global__ void __launch_bounds__(kSimtThreads) simt_kernel(const __grid_constant__ SimtArgs args) {
+__device__ __forceinline__ void simt_body(const SimtArgs& args) {
   extern __shared__ __align__(16) unsigned char smem[];
   for (int k = blockIdx.x; k < args.n_items; k += gridDim.x) {
     // batched launches walk a cost-ordered list: position k -> item id, and
@@ -741,14 +743,40 @@ __global__ void __launch_bounds__(kSimtThreads) simt_kernel(const __grid_constan
     double loss = 0.0;
     const long long t0 = (long long)chunk * I.tiles_per_chunk;
     const long long t1 = (t0 + I.tiles_per_chunk < I.n_tiles) ? t0 + I.tiles_per_chunk : I.n_tiles;
-    for (long long t = t0; t < t1; ++t) {
-      loss += S.tile(t, g);
-      __syncthreads();
-    }
-    if (wacc_on) {
-      __threadfence();
-      __syncthreads();
-      S.wacc_flush(g);
+    if constexpr (Cls::C >= 7) {
+      // FP32 runs of at most kWaccTiles tiles: the FP32 rounding of a
+      // weight's sum stays below kWaccTiles * 2^-24 of its magnitudes at any N
+      long long t = t0;
+      while (t < t1) {
+        const long long r1 = (wacc_on && t1 - t > kWaccTiles) ? t + kWaccTiles : t1;
+        for (; t < r1; ++t) {
+          loss += S.tile(t, g);
+          __syncthreads();
+        }
+        if (wacc_on) {
+          __threadfence();
+          __syncthreads();
+          S.wacc_flush(g);
+          if (t < t1) {
+            __syncthreads();
+            S.wacc_zero();
+            __syncthreads();
+          }
+        }
+      }
+    } else {
+      // smaller channel sets keep every register for the tile and flush
+      // once per chunk; their accumulator serves only nets too wide for
+      // L2-resident FP64 slices
+      for (long long t = t0; t < t1; ++t) {
+        loss += S.tile(t, g);
+        __syncthreads();
+      }
+      if (wacc_on) {
+        __threadfence();
+        __syncthreads();
+        S.wacc_flush(g);
+      }
     }
     // block reduction of the loss partial (fixed order)
     for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
@@ -761,6 +789,24 @@ __global__ void __launch_bounds__(kSimtThreads) simt_kernel(const __grid_constan
     }
     __syncthreads();
   }
+}
+
+template <class Cls, class T>
+__global__ void __launch_bounds__(kSimtThreads) simt_kernel(const __grid_constant__ SimtArgs args) {
+  simt_body<Cls, T>(args);
+}
+
+// Channel sets of 10 or more: their tiles take most of the shared memory
+// with one CTA per SM, so the registers are sized for one.
+template <class Cls, class T>
+__global__ void __launch_bounds__(kSimtThreads, 1) simt_kernel_wide(const __grid_constant__ SimtArgs args) {
+  simt_body<Cls, T>(args);
+}
+
+template <class Cls, class T>
+constexpr auto simt_entry() {
+  if constexpr (Cls::C >= 10) return &simt_kernel_wide<Cls, T>;
+  else return &simt_kernel<Cls, T>;
 }
 
 // Elementwise activation rule on [n][C] FP64 jets (verification hook, Eq. 15).

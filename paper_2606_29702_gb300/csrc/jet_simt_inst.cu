@@ -37,13 +37,13 @@ template <>
 cudaError_t simt_launch_id<JET_CLASS_ID>(bool fp64, const SimtArgs& a, int grid, size_t smem, cudaStream_t s) {
   cudaError_t e;
   if (fp64) {
-    e = prepare(simt_kernel<ThisCls, double>, smem);
+    e = prepare(simt_entry<ThisCls, double>(), smem);
     if (e != cudaSuccess) return e;
-    simt_kernel<ThisCls, double><<<grid, kSimtThreads, smem, s>>>(a);
+    simt_entry<ThisCls, double>()<<<grid, kSimtThreads, smem, s>>>(a);
   } else {
-    e = prepare(simt_kernel<ThisCls, float>, smem);
+    e = prepare(simt_entry<ThisCls, float>(), smem);
     if (e != cudaSuccess) return e;
-    simt_kernel<ThisCls, float><<<grid, kSimtThreads, smem, s>>>(a);
+    simt_entry<ThisCls, float>()<<<grid, kSimtThreads, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -52,13 +52,13 @@ template <>
 cudaError_t simt_max_active_id<JET_CLASS_ID>(bool fp64, size_t smem, int* blocks) {
   cudaError_t e;
   if (fp64) {
-    e = cudaFuncSetAttribute(simt_kernel<ThisCls, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(simt_entry<ThisCls, double>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, simt_kernel<ThisCls, double>, kSimtThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, simt_entry<ThisCls, double>(), kSimtThreads, smem);
   }
-  e = cudaFuncSetAttribute(simt_kernel<ThisCls, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(simt_entry<ThisCls, float>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, simt_kernel<ThisCls, float>, kSimtThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, simt_entry<ThisCls, float>(), kSimtThreads, smem);
 }
 
 template <>
