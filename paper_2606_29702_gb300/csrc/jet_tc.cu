@@ -67,7 +67,8 @@ struct TcPlan {
   int wg_max_items = 0, wg_sms = 0;
 };
 
-// budget of the per-chunk gradient slices (they are updated once per tile)
+// budget of the per-chunk gradient slices (their bias, output-layer and
+// first-layer entries take FP64 adds every tile, so they should stay in L2)
 constexpr double kSliceBudgetBytes = 48.0 * 1024 * 1024;
 
 // ------------------------------------------------------------------ weight-gradient GEMM
