@@ -313,8 +313,9 @@ struct OffW {
 
 // BF16 copies of the weights in the MMA's view: W^l (l = 2..L-1) as a
 // [w][w] block-diagonal matrix of G copies of the wu x wu weights, and the
-// output weights as [G * n_out][w], row s * n_out + o holding W^L[o] in the
-// columns of sub-tile s (G = 1: plain copies)
+// output weights as [128][w]: in every 32-row lane quadrant, row s * n_out + o
+// holds W^L[o] in the columns of sub-tile s (G = 1: plain copies), so that
+// the output rows of D sit in all four TMEM lane quadrants
 __global__ void tc_prep_kernel_v(const float* params, int L, int w, int wu, int n_out, OffW offW, __nv_bfloat16* Wh,
                                  __nv_bfloat16* Wl, __nv_bfloat16* Wlo, long long nh, long long nl) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nh + nl;
@@ -328,9 +329,10 @@ __global__ void tc_prep_kernel_v(const float* params, int L, int w, int wu, int 
       if (Wlo) Wlo[i] = __float2bfloat16_rn(v - __bfloat162float(hi));
     } else {
       const long long r = i - nh;
-      const int row = (int)(r / w), col = (int)(r % w);
+      const int row = (int)(r / w) & 31, col = (int)(r % w);
       const int sub = row / n_out, o = row % n_out;
-      Wl[r] = __float2bfloat16_rn(col / wu == sub ? params[offW.v[L - 1] + (long long)o * wu + col % wu] : 0.f);
+      const bool live = row < (w / wu) * n_out && col / wu == sub;
+      Wl[r] = __float2bfloat16_rn(live ? params[offW.v[L - 1] + (long long)o * wu + col % wu] : 0.f);
     }
   }
 }
@@ -511,7 +513,7 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
     t->scratch_stride += (long long)std::max(0, L - 2) * t->G * t->wu * t->wu * (long long)sizeof(float);
   }
   // workspace
-  const long long nh = (long long)std::max(0, L - 2) * t->w * t->w, nl = (long long)t->G * p->n_out * t->w;
+  const long long nh = (long long)std::max(0, L - 2) * t->w * t->w, nl = 128LL * t->w;
   size_t b_wh = std::max<long long>(nh, 1) * 2, b_wl = nl * 2, b_wlo = t->split3 ? b_wh : 0;
   t->shared_acc = (double)t->grid * p->n_params * 8.0 > kSliceBudgetBytes;
   size_t b_gs = (size_t)(t->shared_acc ? 1 : t->grid) * p->n_params * 8, b_ls = (size_t)t->grid * 8;
@@ -551,7 +553,7 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   const int R = 128 * t->H;
   const int we = t->w;
   bool ok = encode(&t->wmap, t->Wh, we, we, std::max(1, L - 2), R, 3) &&
-            encode(&t->wlmap, t->Wl, we, (cuuint64_t)t->G * p->n_out, 1, 128, 2);
+            encode(&t->wlmap, t->Wl, we, 128, 1, 128, 2);
   if (ok && t->split3) ok = encode(&t->wlomap, t->Wlo, we, we, std::max(1, L - 2), R, 3);
   if (!ok) {
     tc_plan_destroy(t);
@@ -702,7 +704,7 @@ void ensure_store(TcPlan* t, long long N) {
 jet_status prep(const jet_plan_s* p, TcPlan* t, const void* params, cudaStream_t s) {
   OffW ow;
   for (int l = 0; l < p->L; ++l) ow.v[l] = p->off_W[l];
-  const long long nh = (long long)std::max(0, p->L - 2) * t->w * t->w, nl = (long long)t->G * p->n_out * t->w;
+  const long long nh = (long long)std::max(0, p->L - 2) * t->w * t->w, nl = 128LL * t->w;
   int grid = (int)std::min<long long>((nh + nl + 255) / 256, 1024);
   tc_prep_kernel_v<<<grid, 256, 0, s>>>(reinterpret_cast<const float*>(params), p->L, t->w, t->wu, p->n_out, ow,
                                         t->Wh, t->Wl, t->Wlo, nh, nl);

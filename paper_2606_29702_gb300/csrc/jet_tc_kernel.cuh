@@ -96,7 +96,7 @@ __device__ __forceinline__ void tanh_derivs_fast2(f2 z, f2* p) {
 
 struct alignas(64) TcInst {
   CUtensorMap wmap;    // hidden weights bf16 [L-2][w][w]: dims (in, out, layer), box (64, R_W, 1)
-  CUtensorMap wlmap;   // output weights bf16 [n_out][w]: dims (in, out), box (64, 128)
+  CUtensorMap wlmap;   // output weights bf16 [128][w] (rows repeated per lane quadrant): box (64, 128)
   CUtensorMap wlomap;  // low parts of the hidden weights (JET_BF16X3), like wmap
   int L, d, n_out, n_res, w, H, P, cols, cols_pad, top_cols, split3;
   // packing: operand row r holds unit r % wu of sub-tile r / wu; G = w / wu
@@ -405,19 +405,19 @@ struct TcTile {
   }
 
   // UO[o*C + c][s*Pc + n] = D[R1(0)][row s*n_out + o] (+ b^L on the value
-  // channel).  The rows sit in TMEM lanes 0..G*n_out-1, which the warps of
-  // lane quadrant 0 (one per warpgroup) read, splitting the column groups.
+  // channel).  The output weights repeat in every 32-row lane quadrant, so
+  // the rows sit in lanes 0..G*n_out-1 of every quadrant: each warp reads its
+  // own quadrant, and all warps split the column groups.
   __device__ void out_epilogue() {
-    if (q != 0) return;
     float* uo = UO();
-    const int Pc = I.Pc, ng = Pc / 8, nrow = I.G * I.n_out;
-    for (int k = wg; k < C * ng; k += nwg) {
+    const int Pc = I.Pc, ng = Pc / 8, nrow = I.G * I.n_out, lane = tid & 31;
+    for (int k = wg * 4 + q; k < C * ng; k += nwg * 4) {
       const int c = k / ng, g = (k - c * ng) * 8;
       float v[8];
-      tc::tmem_ld8(R1(0) + (uint32_t)(blk(c) * Pc + g), v);
+      tc::tmem_ld8(R1(0) + lane_base() + (uint32_t)(blk(c) * Pc + g), v);
       tc::tmem_wait_ld();
-      if (ul < nrow) {
-        const int sub = ul / I.n_out, o = ul - sub * I.n_out;
+      if (lane < nrow) {
+        const int sub = lane / I.n_out, o = lane - sub * I.n_out;
         const float b = c == 0 ? I.params[I.off_b[I.L - 1] + o] : 0.f;
 #pragma unroll
         for (int j = 0; j < 8; ++j) uo[(o * C + c) * I.P + sub * Pc + g + j] = v[j] + b;
