@@ -175,13 +175,13 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
 # null.  The Helmholtz entry was captured at N = 32768 and scaled by the point
 # count (its traffic is the per-tile store, proportional to N).
 TRAFFIC = {
-    ("ks_2x64x5", "fp32"): (12168704 + 814621184, "f5c4a516bedbe0f9"),
-    ("ks_2x64x5", "bf16"): (872960 + 18830848, "f5c4a516bedbe0f9"),
-    ("ks_2x64x5", "bf16x3"): (1010688 + 30788352, "f5c4a516bedbe0f9"),
-    ("ks_2x64x5", "fp64"): (9929984 + 518699776, "f5c4a516bedbe0f9"),
-    ("ns_psi_3x128x6", "bf16"): (101470464 + 8315597824, "f5c4a516bedbe0f9"),
-    ("helmholtz_3x256x8", "bf16"): ((316041216 + 1837526016) * 32, "f5c4a516bedbe0f9"),
-    ("ensemble_64", "bf16"): (780659456 + 5521017856, "f5c4a516bedbe0f9"),
+    ("ks_2x64x5", "fp32"): (7544064 + 812526592, "6f7531be477c9ee7"),
+    ("ks_2x64x5", "bf16"): (899072 + 18775296, "6f7531be477c9ee7"),
+    ("ks_2x64x5", "bf16x3"): (1098240 + 30745088, "6f7531be477c9ee7"),
+    ("ks_2x64x5", "fp64"): (6326016 + 519921920, "6f7531be477c9ee7"),
+    ("ns_psi_3x128x6", "bf16"): (129651712 + 8846407424, "6f7531be477c9ee7"),
+    ("helmholtz_3x256x8", "bf16"): ((318017024 + 1837484288) * 32, "6f7531be477c9ee7"),
+    ("ensemble_64", "bf16"): (781972736 + 5518700032, "6f7531be477c9ee7"),
 }
 
 
