@@ -148,11 +148,10 @@ void below(const Alpha& a, std::set<Alpha>& out) {
   }
 }
 
-int tile_points(int C, int wmax, bool fp64) {
+int tile_points(int wmax, bool fp64) {
   const int TP = fp64 ? 2 : 4;
   int q = kSimtThreads / wmax;
   if (q < 1) q = 1;
-  (void)C;
   return TP * q;
 }
 
@@ -294,7 +293,7 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
   int wmax = 0;
   for (int l = 1; l < n_layers; ++l) wmax = std::max(wmax, widths[l]);
   const int p8 = JET_FLAG_TILE_GET(flags);
-  p->P = p8 ? 8 * p8 : tile_points(p->C, wmax, p->fp64);
+  p->P = p8 ? 8 * p8 : tile_points(wmax, p->fp64);
   p->S = simt_point_stride(p->C, p->P);
   p->pitch = pitch_for(p->S * p->P, p->fp64);
   p->smem = smem_bytes(p->C, p->P, p->pitch, wmax, n_out, d_in, p->elem);

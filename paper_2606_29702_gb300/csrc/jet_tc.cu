@@ -387,8 +387,6 @@ size_t carve(TcPlan& t, int C, int n_out, int d) {
 }  // namespace
 
 jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& prop, size_t mem_budget, int flags) {
-  (void)mem_budget;
-  (void)flags;
   *out = nullptr;
   if (p->prec == JET_TF32) return tfail(JET_ERR_UNSUPPORTED, "JET_TF32 is not provided by this build");
   const int L = p->L, w = p->widths[1];

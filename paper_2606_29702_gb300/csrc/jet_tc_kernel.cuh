@@ -985,8 +985,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
     if (ii != prev_inst) {
       // zero both activation buffers (and split buffers) once per instance:
       // padding rows and columns must read as zero in every MMA
-      const int R = 128 * I.H;
-      (void)R;
       uint4 z4 = make_uint4(0, 0, 0, 0);
       for (int i = tid; i < I.act_bytes / 16; i += nthr) {
         reinterpret_cast<uint4*>(sm + I.o_a0)[i] = z4;
