@@ -175,13 +175,13 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
 # null.  The Helmholtz entry was captured at N = 32768 and scaled by the point
 # count (its traffic is the per-tile store, proportional to N).
 TRAFFIC = {
-    ("ks_2x64x5", "fp32"): (7544064 + 812526592, "6f7531be477c9ee7"),
-    ("ks_2x64x5", "bf16"): (899072 + 18775296, "6f7531be477c9ee7"),
-    ("ks_2x64x5", "bf16x3"): (1098240 + 30745088, "6f7531be477c9ee7"),
-    ("ks_2x64x5", "fp64"): (6326016 + 519921920, "6f7531be477c9ee7"),
-    ("ns_psi_3x128x6", "bf16"): (129651712 + 8846407424, "6f7531be477c9ee7"),
-    ("helmholtz_3x256x8", "bf16"): ((318017024 + 1837484288) * 32, "6f7531be477c9ee7"),
-    ("ensemble_64", "bf16"): (781972736 + 5518700032, "6f7531be477c9ee7"),
+    ("ks_2x64x5", "fp32"): (11795456 + 814117120, "a56c79dd19dc87eb"),
+    ("ks_2x64x5", "bf16"): (898304 + 18763520, "a56c79dd19dc87eb"),
+    ("ks_2x64x5", "bf16x3"): (1033984 + 30974720, "a56c79dd19dc87eb"),
+    ("ks_2x64x5", "fp64"): (5850624 + 521744896, "a56c79dd19dc87eb"),
+    ("ns_psi_3x128x6", "bf16"): (113568256 + 8253713920, "a56c79dd19dc87eb"),
+    ("helmholtz_3x256x8", "bf16"): ((315457280 + 1837645568) * 32, "a56c79dd19dc87eb"),
+    ("ensemble_64", "bf16"): (767603456 + 5526425600, "a56c79dd19dc87eb"),
 }
 
 
