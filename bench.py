@@ -411,17 +411,22 @@ def time_form(spec, form, X_host, steps, warmup, flush, want_kernel=False, e2e=F
 def run_ensemble(args, rank, ws, local):
     """Batched ensemble: one graph-captured jet_batch_train_step per step."""
     import torch
-    from paper_2606_29702_gb300 import jet, specs
+    from paper_2606_29702_gb300 import autotune, jet, specs
     from paper_2606_29702_gb300 import workloads as wl
     form = args.form or "bf16"
     insts = wl.ensemble(base_seed=100 + 1000 * rank)
     dev = torch.device("cuda")
-    plans = [jet.Plan(specs.by_name(i["family"], **i["coefs"]), i["widths"], form) for i in insts]
     ps = [torch.tensor(wl.pack(i["layers"]), dtype=torch.float32, device=dev) for i in insts]
     ms_ = [torch.zeros_like(p) for p in ps]
     vs = [torch.zeros_like(p) for p in ps]
     xh = [torch.tensor(i["X"], dtype=torch.float32).pin_memory() for i in insts]
     xs = [x.to(dev) for x in xh]
+    # tiles autotuned on the batch itself (CTA shape and tile scale timed as
+    # whole batched launches, cached per batch shape), outside the timed region
+    members = [(specs.by_name(i["family"], **i["coefs"]), i["widths"], p) for i, p in zip(insts, ps)]
+    plans = autotune.batch_plans(members, form, xs)
+    tune = autotune.load_cache().get(autotune.batch_key(members, form), {})
+    tiles = [p.info()["tile_points"] for p in plans]
     n_pts = sum(i["N"] for i in insts)
     loss = torch.empty(len(insts), dtype=torch.float64, device=dev)
     batch = jet.Batch(plans)
@@ -483,7 +488,12 @@ def run_ensemble(args, rank, ws, local):
            "config": {"workload": "ensemble_64", "instances": len(insts), "points_per_replica": n_pts,
                       "widths": sorted(set(i["widths"][1] for i in insts)),
                       "depths": [min(len(i["widths"]) - 2 for i in insts), max(len(i["widths"]) - 2 for i in insts)],
-                      "form": form, "l2": "flushed between steps (2x L2 write, outside the per-step events)",
+                      "form": form,
+                      "tiles": "autotuned on the batch: %s CTA(s)/SM, %g x each shape's default tile (%s points); "
+                               "options timed (ms): %s" % (tune.get("ctas"), tune.get("scale", 1.0),
+                                                          ",".join(str(t) for t in sorted(set(tiles))),
+                                                          tune.get("ms")),
+                      "l2": "flushed between steps (2x L2 write, outside the per-step events)",
                       "step": "jet_batch_train_step of all instances, one CUDA graph replay"},
            "e2e": {"value": ws * n_pts / (e2e_ms * 1e-3), "unit": UNIT,
                    "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in xh)),

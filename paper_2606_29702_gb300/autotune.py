@@ -129,3 +129,100 @@ def plan(spec, widths, precision, path=None, **kw):
         kw.setdefault("mem_budget", STORE_BUDGET)
     kw.setdefault("ctas", t[2])
     return jet.Plan(spec, widths, precision, tile=t[0], **kw)
+
+
+BATCH_PREFIX = "batch|"
+# options of a batched ensemble: (CTA shape, fraction of each member's default
+# tile).  A batch runs one CTA shape and the per-tile weight-gradient schedule.
+BATCH_OPTIONS = ((1, 1.0), (1, 0.5), (2, 1.0), (2, 0.5))
+
+
+def batch_key(members, precision):
+    """Cache key of a batch: its member shapes (in order) and precision."""
+    import hashlib
+    sig = "\n".join(shape_key(spec, widths, precision) for spec, widths, _ in members)
+    return BATCH_PREFIX + hashlib.sha1(sig.encode()).hexdigest()[:20]
+
+
+def _member_plans(members, precision, ctas, scale):
+    """One plan per member: CTA shape `ctas`, tile = `scale` x the shape's
+    default tile (rounded down to a size the plan accepts, else the default)."""
+    plans = []
+    try:
+        for spec, widths, _ in members:
+            base = jet.Plan(spec, widths, precision, ctas=ctas)  # raises if the shape does not fit
+            P = base.info()["tile_points"]
+            if scale >= 1.0:
+                plans.append(base)
+                continue
+            base.close()
+            plan = None
+            t = int(P * scale) // 8 * 8
+            while plan is None and t >= 8:
+                try:
+                    plan = jet.Plan(spec, widths, precision, tile=t, ctas=ctas)
+                except jet.JetError:
+                    t -= 8
+            plans.append(plan or jet.Plan(spec, widths, precision, ctas=ctas))
+    except jet.JetError:
+        for p in plans:
+            p.close()
+        raise
+    return plans
+
+
+def _time_batch(plans, params, X, reps):
+    import torch
+    b = jet.Batch(plans)
+    try:
+        b.backward(params, X)  # warm-up (also first-launch costs)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            b.backward(params, X)
+        e.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / reps
+    finally:
+        b.close()
+
+
+def tune_batch(members, precision, X, reps=3, path=None, timer=None, options=BATCH_OPTIONS):
+    """Time the batched backward of all members (one persistent launch) under
+    every option, cache the fastest under the batch key and return
+    (best option, {option: ms}).  members: list of (spec, widths, params);
+    X: each member's points."""
+    timer = timer or _time_batch
+    params = [p for _, _, p in members]
+    results = {}
+    for ctas, scale in options:
+        try:
+            plans = _member_plans(members, precision, ctas, scale)
+        except jet.JetError:
+            continue  # some member does not fit this CTA shape
+        try:
+            results[(ctas, scale)] = float(timer(plans, params, X, reps))
+        finally:
+            for p in plans:
+                p.close()
+    if not results:
+        raise RuntimeError("no batch option fits every member")
+    best = min(results, key=lambda k: (results[k], -k[1], k[0]))
+    cache = load_cache(path)
+    cache[batch_key(members, precision)] = {"ctas": best[0], "scale": best[1],
+                                            "ms": {"%d,%g" % k: v for k, v in results.items()}}
+    save_cache(cache, path)
+    return best, results
+
+
+def batch_plans(members, precision, X, reps=3, path=None, timer=None):
+    """Plans for a batched ensemble (jet.Batch) with tuned tiles: the batch's
+    cached option, or tune_batch on the members' own points first."""
+    e = load_cache(path).get(batch_key(members, precision))
+    if e is None:
+        (ctas, scale), _ = tune_batch(members, precision, X, reps=reps, path=path, timer=timer)
+    else:
+        ctas, scale = int(e["ctas"]), float(e["scale"])
+    return _member_plans(members, precision, ctas, scale)

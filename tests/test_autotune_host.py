@@ -78,3 +78,52 @@ def test_tune_picks_cta_shape_and_schedule(tmp_path, monkeypatch):
     autotune.tune(sp, [2, 64, 64, 1], "fp32", None, None, path=path, candidates=(8,),
                   timer=lambda plan, p, x, s, reps: 1.0)
     assert FakeShapedPlan.made == [(8, 0, False)]
+
+
+class FakeBatchPlan:
+    """Default tile 64 (one CTA) or 32 (two CTAs); width 256 does not fit two."""
+    made = []
+
+    def __init__(self, spec, widths, precision, tile=None, ctas=0, **kw):
+        if ctas == 2 and widths[1] == 256:
+            raise jet.JetError(3, "two CTAs do not fit")
+        if tile is not None and tile % 16:
+            raise jet.JetError(3, "not a whole number of sub-tiles")
+        self.key = (tile or (32 if ctas == 2 else 64), ctas)
+        FakeBatchPlan.made.append(self.key)
+
+    def info(self):
+        return {"tile_points": self.key[0]}
+
+    def close(self):
+        pass
+
+
+def test_batch_tuning_times_whole_batches(tmp_path, monkeypatch):
+    """tune_batch times the whole batch under every option that fits all
+    members (one CTA shape for all, tiles scaled from each default and rounded
+    down to a tile the plan accepts), caches the fastest under the batch's key,
+    and batch_plans reuses it without timing."""
+    monkeypatch.setattr(jet, "Plan", FakeBatchPlan)
+    path = str(tmp_path / "cache.json")
+    b, a = specs.burgers(0.01), specs.allen_cahn()
+    members = [(b, [2, 32, 32, 1], None), (a, [2, 64, 1], None)]
+    timed = []
+
+    def timer(plans, params, X, reps):
+        keys = tuple(p.key for p in plans)
+        timed.append(keys)
+        return {64: 2.0, 32: 1.0, 16: 3.0}[keys[0][0]] + (0.5 if keys[0][1] == 2 else 0.0)
+
+    best, res = autotune.tune_batch(members, "bf16", None, path=path, timer=timer)
+    # (1, 0.5) -> 32-point tiles, the fastest; (2, 0.5) rounds 16 to a size the plan takes
+    assert best == (1, 0.5) and set(res) == set(autotune.BATCH_OPTIONS)
+    assert ((32, 1), (32, 1)) in timed and ((16, 2), (16, 2)) in timed
+    timed.clear()
+    plans = autotune.batch_plans(members, "bf16", None, path=path, timer=timer)
+    assert timed == [] and [p.key for p in plans] == [(32, 1), (32, 1)]
+    # a member too wide for two CTAs removes those options
+    wide = members + [(b, [2, 256, 256, 1], None)]
+    best, res = autotune.tune_batch(wide, "bf16", None, path=path, timer=timer)
+    assert set(res) == {(1, 1.0), (1, 0.5)} and best == (1, 0.5)
+    assert autotune.batch_key(wide, "bf16") != autotune.batch_key(members, "bf16")
