@@ -122,3 +122,23 @@ def test_autotune_on_gpu(tmp_path):
     g0, l0, _ = jet.Plan(sp, widths, "bf16").backward(p, x)
     torch.cuda.synchronize()
     assert rel_l2(g1.cpu().numpy(), g0.cpu().numpy()) < 1e-5
+
+
+def test_batch_autotune_on_gpu(tmp_path):
+    """tune_batch times whole batched launches under each option that fits;
+    batch_plans builds the chosen plans from the cache, and their batch gives
+    the solo gradients (up to FP32 chunk-sum rounding)."""
+    from paper_2606_29702_gb300 import autotune, jet, specs
+    insts, plans0, ps, xs = _ensemble(2, 2, (1500, 4000), 31)
+    members = [(specs.by_name(i["family"], **i["coefs"]), i["widths"], p) for i, p in zip(insts, ps)]
+    path = str(tmp_path / "tune.json")
+    best, res = autotune.tune_batch(members, "bf16", xs, reps=1, path=path)
+    assert best in res and (1, 1.0) in res
+    plans = autotune.batch_plans(members, "bf16", xs, path=path)
+    grads, losses = jet.Batch(plans).backward(ps, xs)
+    torch.cuda.synchronize()
+    for i in range(len(insts)):
+        g, l, _ = plans0[i].backward(ps[i], xs[i])
+        torch.cuda.synchronize()
+        assert rel_l2(grads[i].cpu().numpy(), g.cpu().numpy()) < 1e-3
+        assert abs(float(losses[i]) - float(l)) <= 1e-5 * abs(float(l))
