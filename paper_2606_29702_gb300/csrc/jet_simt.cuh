@@ -402,40 +402,87 @@ struct SimtTile {
   }
 
   // residual r_c = sum terms - source, loss partial, and (if bwd) ub = dL/du.
+  // Residual r_c = sum of the monomials - source, the loss partial and (bwd)
+  // UB = dL/du.  When the monomial values fit the UB area and 2 r / N the
+  // reduction area: three parallel passes, (point, monomial) products, per
+  // point sums, per (point, output channel) adjoints, each keeping the
+  // operands and order of a per-point loop over the monomials (which is the
+  // fallback).
   __device__ double residual(long long n0, int nvalid, bool bwd) {
-    const int ncol = C * P;
+    const int ncol = C * P, nt = I.n_terms;
     double loss = 0.0;
-    if (bwd)
-      for (int i = threadIdx.x; i < I.n_out * ncol; i += NT) UB[i] = T(0);
-    __syncthreads();
     const T* src = reinterpret_cast<const T*>(I.source);
     T* rout = reinterpret_cast<T*>(I.r_out);
+    const T two_over_n = T(2.0 * I.inv_N);
+    const bool parallel = nt <= I.n_out * C && I.n_res * P * (int)sizeof(T) <= 64 * (int)sizeof(double);
+    if (!parallel) {
+      if (bwd)
+        for (int i = threadIdx.x; i < I.n_out * ncol; i += NT) UB[i] = T(0);
+      __syncthreads();
+      for (int n = threadIdx.x; n < nvalid; n += NT) {
+        T r[kMaxRes];
+        for (int c = 0; c < I.n_res; ++c) r[c] = src ? -src[(n0 + n) * I.n_res + c] : T(0);
+        for (int m = 0; m < nt; ++m) {
+          const DevTerm& tm = I.terms[m];
+          T prod = T(tm.coef);
+          for (int f = 0; f < tm.nfac; ++f) prod *= UO[tm.fac[f] * P + n];
+          r[tm.comp] += prod;
+        }
+        for (int c = 0; c < I.n_res; ++c) {
+          if (rout) rout[(n0 + n) * I.n_res + c] = r[c];
+          loss += (double)r[c] * (double)r[c];
+        }
+        if (bwd)
+          for (int m = 0; m < nt; ++m) {
+            const DevTerm& tm = I.terms[m];
+            const T g = two_over_n * r[tm.comp] * T(tm.coef);
+            for (int f = 0; f < tm.nfac; ++f) {
+              T prod = g;
+              for (int h = 0; h < tm.nfac; ++h)
+                if (h != f) prod *= UO[tm.fac[h] * P + n];
+              UB[tm.fac[f] * P + n] += prod;
+            }
+          }
+      }
+      return loss;
+    }
+    T* prodm = UB;                         // [n_terms][P]
+    T* rg = reinterpret_cast<T*>(RED);     // [n_res][P]: 2 r / N
+    for (int i = threadIdx.x; i < nt * nvalid; i += NT) {
+      const int m = i / nvalid, n = i - m * nvalid;
+      const DevTerm& tm = I.terms[m];
+      T prod = T(tm.coef);
+      for (int f = 0; f < tm.nfac; ++f) prod *= UO[tm.fac[f] * P + n];
+      prodm[m * P + n] = prod;
+    }
+    __syncthreads();
     for (int n = threadIdx.x; n < nvalid; n += NT) {
       T r[kMaxRes];
       for (int c = 0; c < I.n_res; ++c) r[c] = src ? -src[(n0 + n) * I.n_res + c] : T(0);
-      for (int m = 0; m < I.n_terms; ++m) {
-        const DevTerm& tm = I.terms[m];
-        T prod = T(tm.coef);
-        for (int f = 0; f < tm.nfac; ++f) prod *= UO[tm.fac[f] * P + n];
-        r[tm.comp] += prod;
-      }
+      for (int m = 0; m < nt; ++m) r[I.terms[m].comp] += prodm[m * P + n];
       for (int c = 0; c < I.n_res; ++c) {
         if (rout) rout[(n0 + n) * I.n_res + c] = r[c];
         loss += (double)r[c] * (double)r[c];
+        rg[c * P + n] = two_over_n * r[c];
       }
-      if (bwd) {
-        const T two_over_n = T(2.0 * I.inv_N);
-        for (int m = 0; m < I.n_terms; ++m) {
+    }
+    __syncthreads();  // the products in UB are consumed
+    if (!bwd) return loss;
+    for (int i = threadIdx.x; i < I.n_out * ncol; i += NT) {
+      const int k = i / P, n = i - k * P;
+      T acc = T(0);
+      if (n < nvalid)
+        for (int m = 0; m < nt; ++m) {
           const DevTerm& tm = I.terms[m];
-          const T g = two_over_n * r[tm.comp] * T(tm.coef);
           for (int f = 0; f < tm.nfac; ++f) {
-            T prod = g;
+            if (tm.fac[f] != k) continue;
+            T prod = rg[tm.comp * P + n] * T(tm.coef);
             for (int h = 0; h < tm.nfac; ++h)
               if (h != f) prod *= UO[tm.fac[h] * P + n];
-            UB[tm.fac[f] * P + n] += prod;
+            acc += prod;
           }
         }
-      }
+      UB[i] = acc;
     }
     return loss;
   }
