@@ -175,13 +175,13 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
 # null.  The Helmholtz entry was captured at N = 32768 and scaled by the point
 # count (its traffic is the per-tile store, proportional to N).
 TRAFFIC = {
-    ("ks_2x64x5", "fp32"): (11795456 + 814117120, "a56c79dd19dc87eb"),
-    ("ks_2x64x5", "bf16"): (898304 + 18763520, "a56c79dd19dc87eb"),
-    ("ks_2x64x5", "bf16x3"): (1033984 + 30974720, "a56c79dd19dc87eb"),
-    ("ks_2x64x5", "fp64"): (5850624 + 521744896, "a56c79dd19dc87eb"),
-    ("ns_psi_3x128x6", "bf16"): (113568256 + 8253713920, "a56c79dd19dc87eb"),
-    ("helmholtz_3x256x8", "bf16"): ((315457280 + 1837645568) * 32, "a56c79dd19dc87eb"),
-    ("ensemble_64", "bf16"): (767603456 + 5526425600, "a56c79dd19dc87eb"),
+    ("ks_2x64x5", "fp32"): (14011136 + 815148032, "21a6eab2adb98844"),
+    ("ks_2x64x5", "bf16"): (904960 + 18807040, "21a6eab2adb98844"),
+    ("ks_2x64x5", "bf16x3"): (1047552 + 30708224, "21a6eab2adb98844"),
+    ("ks_2x64x5", "fp64"): (11233280 + 533176576, "21a6eab2adb98844"),
+    ("ns_psi_3x128x6", "bf16"): (99983360 + 8236320512, "21a6eab2adb98844"),
+    ("helmholtz_3x256x8", "bf16"): ((316999680 + 1837413376) * 32, "21a6eab2adb98844"),
+    ("ensemble_64", "bf16"): (796114432 + 5516969472, "21a6eab2adb98844"),
 }
 
 
