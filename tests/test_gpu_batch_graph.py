@@ -142,3 +142,33 @@ def test_batch_autotune_on_gpu(tmp_path):
         torch.cuda.synchronize()
         assert rel_l2(grads[i].cpu().numpy(), g.cpu().numpy()) < 1e-3
         assert abs(float(losses[i]) - float(l)) <= 1e-5 * abs(float(l))
+
+
+def test_simt_batch_with_fp32_accumulator():
+    """FP32 SIMT members wide enough that their FP64 slices leave L2 add their
+    weight gradients in per-CTA FP32 accumulators; in a batch, every chunk item
+    zeroes and flushes its own, and the gradients match the solo runs and the
+    oracle."""
+    import oracle
+    from oracle import residuals as R
+    from paper_2606_29702_gb300 import jet, specs
+    sp = specs.ns_psi(0.01)
+    widths = [3, 128, 128, 128, 128, 2]
+    plans, ps, xs, refs = [], [], [], []
+    for k, n in enumerate((97, 180)):
+        layers = wl.xavier_layers(widths, 40 + k, bias_std=0.1)
+        X = wl.points([(0, 1)] * 3, n, 50 + k)
+        plans.append(jet.Plan(sp, widths, "fp32"))
+        ps.append(torch.tensor(wl.pack(layers), dtype=torch.float32, device="cuda"))
+        xs.append(torch.tensor(X, dtype=torch.float32, device="cuda"))
+        refs.append(oracle.loss_and_grad(R.by_name("ns_psi", nu=0.01), layers, X))
+    assert all(p.info()["wgrad_chunk_fp32"] == 1 for p in plans)
+    grads, losses = jet.Batch(plans).backward(ps, xs)
+    torch.cuda.synchronize()
+    for i in range(2):
+        g, l, _ = plans[i].backward(ps[i], xs[i])
+        torch.cuda.synchronize()
+        assert rel_l2(grads[i].cpu().numpy(), g.cpu().numpy()) < 1e-6
+        L, _, g_ref = refs[i]
+        assert rel_l2(grads[i].cpu().double().numpy(), wl.pack(g_ref)) < 1e-5
+        assert abs(float(losses[i]) - L) <= 1e-5 * abs(L)
