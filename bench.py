@@ -498,7 +498,7 @@ def run_ensemble(args, rank, ws, local):
            "e2e": {"value": ws * n_pts / (e2e_ms * 1e-3), "unit": UNIT,
                    "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in xh)),
                    "d2h_bytes_per_step": int(lh.numel() * lh.element_size())},
-           "gpu_launches": (len(insts) + 2) * args.steps, "roofline": roof, "clocks": clk, "cpu_baseline": None}
+           "gpu_launches": 3 * args.steps, "roofline": roof, "clocks": clk, "cpu_baseline": None}
     if rank == 0:
         print(json.dumps(out))
 

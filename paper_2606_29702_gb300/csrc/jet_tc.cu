@@ -311,29 +311,60 @@ struct OffW {
   long long v[kMaxLayers];
 };
 
+// One plan's weight preparation: elements [start, start + nh + nl) of a
+// (batched) preparation launch.
+struct PrepJob {
+  const float* params;
+  OffW offW;
+  __nv_bfloat16* Wh;
+  __nv_bfloat16* Wl;
+  __nv_bfloat16* Wlo;
+  long long nh, nl, start;
+  int L, w, wu, n_out;
+};
+
 // BF16 copies of the weights in the MMA's view: W^l (l = 2..L-1) as a
 // [w][w] block-diagonal matrix of G copies of the wu x wu weights, and the
 // output weights as [128][w]: in every 32-row lane quadrant, row s * n_out + o
 // holds W^L[o] in the columns of sub-tile s (G = 1: plain copies), so that
-// the output rows of D sit in all four TMEM lane quadrants
-__global__ void tc_prep_kernel_v(const float* params, int L, int w, int wu, int n_out, OffW offW, __nv_bfloat16* Wh,
-                                 __nv_bfloat16* Wl, __nv_bfloat16* Wlo, long long nh, long long nl) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nh + nl;
+// the output rows of D sit in all four TMEM lane quadrants.  Element i < nh of
+// the job is a hidden weight, the rest output weights.
+__device__ __forceinline__ void prep_element(const PrepJob& j, long long i) {
+  const int w = j.w, wu = j.wu;
+  if (i < j.nh) {
+    const long long l = i / ((long long)w * w), r = i % ((long long)w * w);
+    const int row = (int)(r / w), col = (int)(r % w);
+    const float v = row / wu == col / wu ? j.params[j.offW.v[l + 1] + (long long)(row % wu) * wu + col % wu] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    j.Wh[i] = hi;
+    if (j.Wlo) j.Wlo[i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  } else {
+    const long long r = i - j.nh;
+    const int row = (int)(r / w) & 31, col = (int)(r % w);
+    const int sub = row / j.n_out, o = row % j.n_out;
+    const bool live = row < (w / wu) * j.n_out && col / wu == sub;
+    j.Wl[r] = __float2bfloat16_rn(live ? j.params[j.offW.v[j.L - 1] + (long long)o * wu + col % wu] : 0.f);
+  }
+}
+
+__global__ void tc_prep_kernel_v(const PrepJob j) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < j.nh + j.nl;
+       i += (long long)gridDim.x * blockDim.x)
+    prep_element(j, i);
+}
+
+// all plans of a batch in one launch: element i belongs to the last job
+// whose start is <= i (jobs ordered by start)
+__global__ void tc_prep_batch_kernel(const PrepJob* jobs, int n, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    if (i < nh) {
-      const long long l = i / ((long long)w * w), r = i % ((long long)w * w);
-      const int row = (int)(r / w), col = (int)(r % w);
-      const float v = row / wu == col / wu ? params[offW.v[l + 1] + (long long)(row % wu) * wu + col % wu] : 0.f;
-      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      Wh[i] = hi;
-      if (Wlo) Wlo[i] = __float2bfloat16_rn(v - __bfloat162float(hi));
-    } else {
-      const long long r = i - nh;
-      const int row = (int)(r / w) & 31, col = (int)(r % w);
-      const int sub = row / n_out, o = row % n_out;
-      const bool live = row < (w / wu) * n_out && col / wu == sub;
-      Wl[r] = __float2bfloat16_rn(live ? params[offW.v[L - 1] + (long long)o * wu + col % wu] : 0.f);
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (jobs[mid].start <= i) lo = mid;
+      else hi = mid - 1;
     }
+    prep_element(jobs[lo], i - jobs[lo].start);
   }
 }
 
@@ -699,13 +730,28 @@ void ensure_store(TcPlan* t, long long N) {
   }
 }
 
+PrepJob prep_job(const jet_plan_s* p, const TcPlan* t, const void* params, long long start) {
+  PrepJob j;
+  memset(&j, 0, sizeof(j));
+  j.params = reinterpret_cast<const float*>(params);
+  for (int l = 0; l < p->L; ++l) j.offW.v[l] = p->off_W[l];
+  j.Wh = t->Wh;
+  j.Wl = t->Wl;
+  j.Wlo = t->Wlo;
+  j.nh = (long long)std::max(0, p->L - 2) * t->w * t->w;
+  j.nl = 128LL * t->w;
+  j.start = start;
+  j.L = p->L;
+  j.w = t->w;
+  j.wu = t->wu;
+  j.n_out = p->n_out;
+  return j;
+}
+
 jet_status prep(const jet_plan_s* p, TcPlan* t, const void* params, cudaStream_t s) {
-  OffW ow;
-  for (int l = 0; l < p->L; ++l) ow.v[l] = p->off_W[l];
-  const long long nh = (long long)std::max(0, p->L - 2) * t->w * t->w, nl = 128LL * t->w;
-  int grid = (int)std::min<long long>((nh + nl + 255) / 256, 1024);
-  tc_prep_kernel_v<<<grid, 256, 0, s>>>(reinterpret_cast<const float*>(params), p->L, t->w, t->wu, p->n_out, ow,
-                                        t->Wh, t->Wl, t->Wlo, nh, nl);
+  const PrepJob j = prep_job(p, t, params, 0);
+  int grid = (int)std::min<long long>((j.nh + j.nl + 255) / 256, 1024);
+  tc_prep_kernel_v<<<grid, 256, 0, s>>>(j);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? JET_OK : tcuda(e, "tc prep launch");
 }
@@ -881,6 +927,8 @@ struct TcBatch {
   int* h_items = nullptr;
   ReduceJob* d_jobs = nullptr;
   ReduceJob* h_jobs = nullptr;
+  PrepJob* d_prep = nullptr;  // weight preparation of every member, one launch
+  PrepJob* h_prep = nullptr;
   double* grad_slices = nullptr;
   double* loss_slices = nullptr;
   std::vector<long long> slice_off;
@@ -930,6 +978,8 @@ jet_status tc_batch_create(const std::vector<jet_plan_s*>& plans, TcBatch** out)
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_items, sizeof(int) * 2 * b->max_items);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_jobs, sizeof(ReduceJob) * b->n);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_jobs, sizeof(ReduceJob) * b->n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_prep, sizeof(PrepJob) * b->n);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_prep, sizeof(PrepJob) * b->n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->grad_slices, sizeof(double) * std::max<long long>(slices, 1));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->loss_slices, sizeof(double) * b->max_items);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->scratch, (size_t)b->grid * std::max<long long>(b->scratch_stride, 16));
@@ -941,6 +991,7 @@ jet_status tc_batch_create(const std::vector<jet_plan_s*>& plans, TcBatch** out)
     return tcuda(e, "batch workspace");
   }
   memset(b->h_insts, 0, sizeof(TcInst) * b->n);
+  memset(b->h_prep, 0, sizeof(PrepJob) * b->n);
   *out = b;
   return JET_OK;
 }
@@ -953,6 +1004,8 @@ void tc_batch_destroy(TcBatch* b) {
   cudaFreeHost(b->h_items);
   cudaFree(b->d_jobs);
   cudaFreeHost(b->h_jobs);
+  cudaFree(b->d_prep);
+  cudaFreeHost(b->h_prep);
   cudaFree(b->grad_slices);
   cudaFree(b->loss_slices);
   cudaFree(b->scratch);
@@ -974,9 +1027,12 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
     if (plans[i]->has_source != (source && source[i])) return tfail(JET_ERR_INVALID, "source does not match spec");
     total_tiles += (N[i] + plans[i]->tcp->P - 1) / plans[i]->tcp->P;
   }
+  // weight preparation of every member: one launch over all their elements
+  std::vector<PrepJob> prep_jobs(n);
+  long long prep_total = 0;
   for (int i = 0; i < n; ++i) {
-    jet_status st = prep(plans[i], plans[i]->tcp, params[i], s);
-    if (st != JET_OK) return st;
+    prep_jobs[i] = prep_job(plans[i], plans[i]->tcp, params[i], prep_total);
+    prep_total += prep_jobs[i].nh + prep_jobs[i].nl;
   }
   // work list: about four items per CTA, cost-ordered, largest first
   const long long target = std::max<long long>(1, (total_tiles + 4LL * b->grid - 1) / (4LL * b->grid));
@@ -1018,12 +1074,14 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
   }();
   // upload the descriptors only when they changed; wait for the previous
   // upload to have read the staging buffers before rewriting them
-  bool same = b->have_prev && b->n_items == base && memcmp(b->h_insts, insts.data(), sizeof(TcInst) * n) == 0;
+  bool same = b->have_prev && b->n_items == base && memcmp(b->h_insts, insts.data(), sizeof(TcInst) * n) == 0 &&
+              memcmp(b->h_prep, prep_jobs.data(), sizeof(PrepJob) * n) == 0;
   if (same)
     for (int k = 0; k < base && same; ++k) same = b->h_items[k] == cost[k].second && b->h_items[base + k] == inst_of[k];
   if (!same) {
     if (b->have_prev && !capturing) cudaEventSynchronize(b->copied);
     memcpy(b->h_insts, insts.data(), sizeof(TcInst) * n);
+    memcpy(b->h_prep, prep_jobs.data(), sizeof(PrepJob) * n);
     for (int k = 0; k < base; ++k) {
       b->h_items[k] = cost[k].second;
       b->h_items[base + k] = inst_of[k];
@@ -1031,9 +1089,16 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
     b->n_items = base;
     cudaError_t e = cudaMemcpyAsync(b->d_insts, b->h_insts, sizeof(TcInst) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_items, b->h_items, sizeof(int) * 2 * base, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_prep, b->h_prep, sizeof(PrepJob) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !capturing) e = cudaEventRecord(b->copied, s);
     if (e != cudaSuccess) return tcuda(e, "batch descriptor upload");
     b->have_prev = b->have_prev || !capturing;
+  }
+  {
+    const int pgrid = (int)std::min<long long>((prep_total + 255) / 256, 2048);
+    tc_prep_batch_kernel<<<pgrid, 256, 0, s>>>(b->d_prep, n, prep_total);
+    cudaError_t pe = cudaGetLastError();
+    if (pe != cudaSuccess) return tcuda(pe, "batched weight preparation");
   }
   TcArgs a;
   memset(&a, 0, sizeof(a));
