@@ -34,31 +34,61 @@ cudaError_t launch_transpose_weights(const DevInstance& in, bool fp64, void* Wt,
 }
 
 // Adam (Kingma & Ba 2015) with beta1 = 0.9, beta2 = 0.999, eps = 1e-8; the
-// paper fixes only the learning rate (1e-3).
+// paper fixes only the learning rate (1e-3).  The update runs in the value
+// type of the parameters (FP32 for the FP32 and BF16 forms); the gradient it
+// takes is the FP64 sum over chunks.
 struct AdamConst {
   double lr, beta1, beta2, eps, bc1, bc2;
+  float lr_f, beta1_f, beta2_f, eps_f, bc1_f, bc2_f;
 };
 
+// One block takes 32 consecutive parameters (lanes over parameters, so every
+// slice row is read coalesced); its 8 warps sum every 8th chunk slice in FP64
+// and warp 0 adds the 8 partials in a fixed order: deterministic, and enough
+// blocks to fill the GPU when there are many chunks.
+constexpr int kRedWarps = 8;
+
 template <class T, bool ADAM>
-__global__ void reduce_kernel(const __grid_constant__ ReduceJob job0, const ReduceJob* jobs, AdamConst ac) {
+__global__ void __launch_bounds__(32 * kRedWarps) reduce_kernel(const __grid_constant__ ReduceJob job0,
+                                                                const ReduceJob* jobs, AdamConst ac) {
   const ReduceJob& J = jobs ? jobs[blockIdx.y] : job0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < J.n_params;
-       p += (long long)gridDim.x * blockDim.x) {
+  __shared__ double part[kRedWarps][32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int gc = J.grad_chunks > 0 ? J.grad_chunks : J.n_chunks;
+  for (long long p0 = (long long)blockIdx.x * 32; p0 < J.n_params; p0 += (long long)gridDim.x * 32) {
+    const long long p = p0 + lane;
     double g = 0.0;
-    const int gc = J.grad_chunks > 0 ? J.grad_chunks : J.n_chunks;
-    for (int c = 0; c < gc; ++c) g += J.grad_slices[(long long)c * J.n_params + p];
-    if (J.grad_out) reinterpret_cast<T*>(J.grad_out)[p] = (T)g;
-    if (ADAM) {
-      T* th = reinterpret_cast<T*>(J.params);
-      T* m = reinterpret_cast<T*>(J.m);
-      T* v = reinterpret_cast<T*>(J.v);
-      const double mm = ac.beta1 * (double)m[p] + (1.0 - ac.beta1) * g;
-      const double vv = ac.beta2 * (double)v[p] + (1.0 - ac.beta2) * g * g;
-      m[p] = (T)mm;
-      v[p] = (T)vv;
-      const double mhat = mm / ac.bc1, vhat = vv / ac.bc2;
-      th[p] = (T)((double)th[p] - ac.lr * mhat / (sqrt(vhat) + ac.eps));
+    if (p < J.n_params)
+      for (int c = wp; c < gc; c += kRedWarps) g += J.grad_slices[(long long)c * J.n_params + p];
+    part[wp][lane] = g;
+    __syncthreads();
+    if (wp == 0 && p < J.n_params) {
+      g = 0.0;
+#pragma unroll
+      for (int w = 0; w < kRedWarps; ++w) g += part[w][lane];
+      if (J.grad_out) reinterpret_cast<T*>(J.grad_out)[p] = (T)g;
+      if (ADAM) {
+        T* th = reinterpret_cast<T*>(J.params);
+        T* m = reinterpret_cast<T*>(J.m);
+        T* v = reinterpret_cast<T*>(J.v);
+        if constexpr (sizeof(T) == 4) {
+          const float gf = (float)g;
+          const float mm = ac.beta1_f * m[p] + (1.0f - ac.beta1_f) * gf;
+          const float vv = ac.beta2_f * v[p] + (1.0f - ac.beta2_f) * gf * gf;
+          m[p] = mm;
+          v[p] = vv;
+          th[p] = th[p] - ac.lr_f * (mm / ac.bc1_f) / (sqrtf(vv / ac.bc2_f) + ac.eps_f);
+        } else {
+          const double mm = ac.beta1 * (double)m[p] + (1.0 - ac.beta1) * g;
+          const double vv = ac.beta2 * (double)v[p] + (1.0 - ac.beta2) * g * g;
+          m[p] = (T)mm;
+          v[p] = (T)vv;
+          const double mhat = mm / ac.bc1, vhat = vv / ac.bc2;
+          th[p] = (T)((double)th[p] - ac.lr * mhat / (sqrt(vhat) + ac.eps));
+        }
+      }
     }
+    __syncthreads();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && J.loss_out) {
     double s = 0.0;
@@ -76,17 +106,24 @@ cudaError_t launch_reduce(const ReduceJob* dev_jobs, const ReduceJob& job0, int 
   ac.eps = 1e-8;
   ac.bc1 = 1.0 - pow(ac.beta1, (double)(step < 1 ? 1 : step));
   ac.bc2 = 1.0 - pow(ac.beta2, (double)(step < 1 ? 1 : step));
-  long long gx = (max_params + 255) / 256;
-  if (gx > 1024) gx = 1024;
+  ac.lr_f = lr;
+  ac.beta1_f = 0.9f;
+  ac.beta2_f = 0.999f;
+  ac.eps_f = 1e-8f;
+  ac.bc1_f = (float)ac.bc1;
+  ac.bc2_f = (float)ac.bc2;
+  long long gx = (max_params + 31) / 32;
+  if (gx > 4096) gx = 4096;
   if (gx < 1) gx = 1;
   dim3 grid((unsigned)gx, (unsigned)(n > 0 ? n : 1));
   const ReduceJob* jobs = n == 1 ? nullptr : dev_jobs;
+  const int threads = 32 * kRedWarps;
   if (fp64) {
-    if (adam) reduce_kernel<double, true><<<grid, 256, 0, s>>>(job0, jobs, ac);
-    else reduce_kernel<double, false><<<grid, 256, 0, s>>>(job0, jobs, ac);
+    if (adam) reduce_kernel<double, true><<<grid, threads, 0, s>>>(job0, jobs, ac);
+    else reduce_kernel<double, false><<<grid, threads, 0, s>>>(job0, jobs, ac);
   } else {
-    if (adam) reduce_kernel<float, true><<<grid, 256, 0, s>>>(job0, jobs, ac);
-    else reduce_kernel<float, false><<<grid, 256, 0, s>>>(job0, jobs, ac);
+    if (adam) reduce_kernel<float, true><<<grid, threads, 0, s>>>(job0, jobs, ac);
+    else reduce_kernel<float, false><<<grid, threads, 0, s>>>(job0, jobs, ac);
   }
   return cudaGetLastError();
 }
