@@ -175,13 +175,13 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
 # null.  The Helmholtz entry was captured at N = 32768 and scaled by the point
 # count (its traffic is the per-tile store, proportional to N).
 TRAFFIC = {
-    ("ks_2x64x5", "fp32"): (14011136 + 815148032, "21a6eab2adb98844"),
-    ("ks_2x64x5", "bf16"): (904960 + 18807040, "21a6eab2adb98844"),
-    ("ks_2x64x5", "bf16x3"): (1047552 + 30708224, "21a6eab2adb98844"),
-    ("ks_2x64x5", "fp64"): (11233280 + 533176576, "21a6eab2adb98844"),
-    ("ns_psi_3x128x6", "bf16"): (99983360 + 8236320512, "21a6eab2adb98844"),
-    ("helmholtz_3x256x8", "bf16"): ((316999680 + 1837413376) * 32, "21a6eab2adb98844"),
-    ("ensemble_64", "bf16"): (796114432 + 5516969472, "21a6eab2adb98844"),
+    ("ks_2x64x5", "fp32"): (14095616 + 806919424, "f09d51b33d7b8077"),
+    ("ks_2x64x5", "bf16"): (904192 + 18787584, "f09d51b33d7b8077"),
+    ("ks_2x64x5", "bf16x3"): (1049344 + 31012608, "f09d51b33d7b8077"),
+    ("ks_2x64x5", "fp64"): (10806784 + 532503808, "f09d51b33d7b8077"),
+    ("ns_psi_3x128x6", "bf16"): (100244992 + 8230092800, "f09d51b33d7b8077"),
+    ("helmholtz_3x256x8", "bf16"): ((316963072 + 1837615360) * 32, "f09d51b33d7b8077"),
+    ("ensemble_64", "bf16"): (794983680 + 5520442368, "f09d51b33d7b8077"),
 }
 
 
