@@ -3,15 +3,24 @@
 One step = one full pass of the hot path over one batch of collocation points:
 jet forward (all channels, all layers), residual, loss, residual adjoint,
 reverse sweep to the parameter gradient, FP64 reduction and the Adam update
-(jet_train_step).  Default workload: Kuramoto-Sivashinsky, 2->64x5->1 tanh
-MLP, N = 65536 points uniform on [0, 2pi] x [0, 1], plain FP32 form (the
-configuration the points/s metric is quoted on).  Other precision forms of the
-same workload are timed beside it under "forms".
+(jet_train_step).
 
-``--workload ensemble_64`` times the batched form instead: 64 independent
-PINNs (32 Burgers, 32 Allen-Cahn; widths 32/64/128, 3-8 hidden layers, N_i in
-[2048, 65536]) trained together by one persistent BF16 launch per step,
-captured in a CUDA graph and replayed; points/s counts every instance's points.
+Headline (default): 3-D Helmholtz, 3->256x8->1 tanh MLP, N = 1048576 points
+uniform on [-1,1]^3, BF16 tensor-core form, Adam lr 1e-3 -- the largest
+single-GPU configuration.  Beside it, in the same run and under named keys
+("workloads"): the other schedule of the same workload, its plain FP32 form,
+the stream-function Navier-Stokes 3->128x6->2 (BF16, BF16X3, FP32), the
+Kuramoto-Sivashinsky 2->64x5->1 (FP32, BF16, BF16X3), the FP64 Burgers
+2->20x4->1 and the 64-instance batched ensemble in BF16 and in plain FP32.
+
+``--workload ensemble_64`` makes the batched form the headline: 64
+independent PINNs (32 Burgers, 32 Allen-Cahn; widths 32/64/128, 3-8 hidden
+layers, N_i in [2048, 65536]) trained together by one persistent launch per
+step, captured in a CUDA graph whose Adam step counter lives on the device.
+
+``--train K`` runs K Adam steps of the headline workload after 20 warm-up
+steps (Sec. 3.1.1: 1000 steps, lr 1e-3) and reports the time per step and the
+loss history.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs an independent replica of the workload (the
@@ -39,17 +48,31 @@ L2_BYTES = 129 * 1024 * 1024
 STORE_BUDGET = 96 << 30  # HBM the tensor-core forms may use for the weight-gradient store
 
 
+HEADLINE = "helmholtz_3x256x8"
+# the named workloads timed beside the headline: (workload, form, schedule)
+SIDE = [("helmholtz_3x256x8", "bf16", "store"), ("helmholtz_3x256x8", "bf16", "tile"),
+        ("helmholtz_3x256x8", "fp32", "tile"),
+        ("ns_psi_3x128x6", "bf16", "tile"), ("ns_psi_3x128x6", "bf16x3", "tile"), ("ns_psi_3x128x6", "fp32", "tile"),
+        ("ks_2x64x5", "fp32", "tile"), ("ks_2x64x5", "bf16", "tile"), ("ks_2x64x5", "bf16x3", "tile"),
+        ("burgers_2x20x4", "fp64", "tile"),
+        ("ensemble_64", "bf16", "tile"), ("ensemble_64", "fp32", "tile")]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ks_2x64x5")
+    ap.add_argument("--workload", default=HEADLINE)
     ap.add_argument("--form", default=None, help="precision form of the headline (default: the workload's)")
-    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--schedule", default=None, choices=["tile", "store"],
+                    help="weight-gradient schedule of a tensor-core headline (default: the workload's)")
+    ap.add_argument("--no-forms", action="store_true", help="time the headline only")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="0 skips the oracle leg")
     ap.add_argument("--n", type=int, default=None, help="override the workload's point count (profiling)")
+    ap.add_argument("--train", type=int, default=0, help="K > 0: a K-step Adam training run of the headline")
+    ap.add_argument("--history", default=None, help="--train: write the loss history (JSON) here")
     return ap.parse_args()
 
 
@@ -169,19 +192,13 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the same workload and
-# form; (workload, form) -> (bytes per launch, hash of the kernel sources the
-# counters were taken on).  A different hash (the kernels changed since) gives
-# null.  The Helmholtz entry was captured at N = 32768 and scaled by the point
-# count (its traffic is the per-tile store, proportional to N).
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the same workload, form
+# and schedule; (workload, form, schedule) -> (bytes per launch, hash of the
+# kernel sources the counters were taken on).  A different hash (the kernels
+# changed since) gives null.  Entries taken on a smaller N than the workload's
+# are scaled by the point count where the traffic is per tile (stated in the
+# profile summaries).
 TRAFFIC = {
-    ("ks_2x64x5", "fp32"): (14095616 + 806919424, "f09d51b33d7b8077"),
-    ("ks_2x64x5", "bf16"): (904192 + 18787584, "f09d51b33d7b8077"),
-    ("ks_2x64x5", "bf16x3"): (1049344 + 31012608, "f09d51b33d7b8077"),
-    ("ks_2x64x5", "fp64"): (10806784 + 532503808, "f09d51b33d7b8077"),
-    ("ns_psi_3x128x6", "bf16"): (100244992 + 8230092800, "f09d51b33d7b8077"),
-    ("helmholtz_3x256x8", "bf16"): ((316963072 + 1837615360) * 32, "f09d51b33d7b8077"),
-    ("ensemble_64", "bf16"): (794983680 + 5520442368, "f09d51b33d7b8077"),
 }
 
 
@@ -196,8 +213,8 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_for(workload, form):
-    e = TRAFFIC.get((workload, form))
+def traffic_for(workload, form, schedule="tile"):
+    e = TRAFFIC.get((workload, form, schedule))
     return e[0] if e is not None and e[1] == kernel_source_hash() else None
 
 
@@ -333,17 +350,38 @@ def gpu_sample(spec, form, X, layers, src):
 
 
 # ------------------------------------------------------------------ ours
-def time_form(spec, form, X_host, steps, warmup, flush, want_kernel=False, e2e=False):
-    """Time `steps` train steps of one precision form; returns a dict."""
-    import torch
+DTYPES = {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "tf32": "tf32", "bf16x3": "bf16x3"}
+
+
+def default_schedule(spec, form):
+    """Weight-gradient schedule of a tensor-core form: the store (layer inputs
+    and adjoints of every tile in HBM, one weight-gradient GEMM per layer) for
+    width-256 layers, where it measured 3x faster; per-tile flushes otherwise."""
+    return "store" if form in ("bf16", "bf16x3") and max(spec["widths"][1:-1]) >= 256 else "tile"
+
+
+def launches_per_step(form, schedule, batched=False, dev_counter=False):
+    """Kernels of ours one train step launches (memsets excluded)."""
+    if form in ("fp32", "fp64"):
+        n = 3  # weight transposition (one per member when batched), fused SIMT kernel, reduce + Adam
+    else:
+        n = 3 if schedule == "tile" else 5  # weight prep, fused tcgen05 kernel, [wgrad GEMM, wgrad sum], reduce
+    return n + (1 if dev_counter else 0)
+
+
+def make_plan(spec, form, schedule):
     from paper_2606_29702_gb300 import jet, specs
-    from paper_2606_29702_gb300 import workloads as wl
     sp = specs.by_name(spec["family"], **spec["coefs"])
-    # wide tensor-core layers keep layer inputs and adjoints in HBM (store mode,
-    # up to STORE_BUDGET bytes) so that the weight gradients run as one GEMM per
-    # layer; narrower ones flush per tile (the faster choice measured there)
-    store = form in ("bf16", "bf16x3", "tf32") and max(spec["widths"][1:-1]) >= 256
-    plan = jet.Plan(sp, spec["widths"], form, store=store, mem_budget=STORE_BUDGET if store else 0)
+    kw = dict(store=True, mem_budget=STORE_BUDGET) if schedule == "store" else {}
+    return sp, jet.Plan(sp, spec["widths"], form, **kw)
+
+
+def time_form(spec, form, X_host, steps, warmup, flush, want_kernel=False, e2e=False, schedule="tile"):
+    """Time `steps` train steps of one precision form and schedule; returns a dict."""
+    import torch
+    from paper_2606_29702_gb300 import specs
+    from paper_2606_29702_gb300 import workloads as wl
+    sp, plan = make_plan(spec, form, schedule)
     dt = plan.dtype
     dev = torch.device("cuda")
     layers = wl.xavier_layers(spec["widths"], spec["seed_par"])
@@ -376,7 +414,8 @@ def time_form(spec, form, X_host, steps, warmup, flush, want_kernel=False, e2e=F
         step += 1
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
-    out = {"ms_per_step": ms, "value": X_host.shape[0] / (ms * 1e-3), "info": plan.info()}
+    out = {"ms_per_step": ms, "value": X_host.shape[0] / (ms * 1e-3), "info": plan.info(), "schedule": schedule,
+           "loss": float(loss)}
     if want_kernel:
         n, kms = plan.profile_read()
         plan.profile(False)
@@ -408,12 +447,13 @@ def time_form(spec, form, X_host, steps, warmup, flush, want_kernel=False, e2e=F
     return out
 
 
-def run_ensemble(args, rank, ws, local):
-    """Batched ensemble: one graph-captured jet_batch_train_step per step."""
+def time_ensemble(form, steps, warmup, rank=0, e2e=True):
+    """Batched ensemble: one graph-captured jet_batch_train_step_dev per step
+    (the Adam step counter lives on the device, so every replay is the next
+    step).  Returns a dict with the per-step time and the points of a replica."""
     import torch
     from paper_2606_29702_gb300 import autotune, jet, specs
     from paper_2606_29702_gb300 import workloads as wl
-    form = args.form or "bf16"
     insts = wl.ensemble(base_seed=100 + 1000 * rank)
     dev = torch.device("cuda")
     ps = [torch.tensor(wl.pack(i["layers"]), dtype=torch.float32, device=dev) for i in insts]
@@ -429,78 +469,123 @@ def run_ensemble(args, rank, ws, local):
     tiles = [p.info()["tile_points"] for p in plans]
     n_pts = sum(i["N"] for i in insts)
     loss = torch.empty(len(insts), dtype=torch.float64, device=dev)
+    ctr = torch.zeros(1, dtype=torch.int64, device=dev)
     batch = jet.Batch(plans)
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    W = max(args.warmup, 3)
+    W = max(warmup, 3)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
         for k in range(W):
-            batch.train_step(ps, ms_, vs, k + 1, 1e-3, xs, loss=loss, stream=s)
+            batch.train_step_dev(ps, ms_, vs, ctr, 1e-3, xs, loss=loss, stream=s)
     torch.cuda.synchronize()
     # one step captured as a CUDA graph (descriptor uploads, weight preparation,
-    # the persistent batched kernel and the batched FP64 reduce + Adam)
+    # the persistent batched kernel, the batched FP64 reduce + Adam and the
+    # step-counter advance)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
-        batch.train_step(ps, ms_, vs, W + 1, 1e-3, xs, loss=loss, stream=s)
+        batch.train_step_dev(ps, ms_, vs, ctr, 1e-3, xs, loss=loss, stream=s)
     torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        flush_buf.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    out = {"ms_per_step": ms, "value": n_pts / (ms * 1e-3), "n_pts": n_pts, "insts": insts, "tune": tune,
+           "tiles": tiles, "adam_steps_taken": int(ctr.item()), "loss_mean": float(loss.mean())}
+    if e2e:
+        # end to end: pinned host points in, losses out, every step
+        lh = torch.empty(len(insts), dtype=torch.float64).pin_memory()
+        evs = []
+        for _ in range(steps):
+            flush_buf.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for xd, xp in zip(xs, xh):
+                xd.copy_(xp, non_blocking=True)
+            g.replay()
+            lh.copy_(loss, non_blocking=True)
+            b.record()
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        out["e2e_ms"] = sum(a.elapsed_time(b) for a, b in evs) / steps
+        out["h2d"] = int(sum(x.numel() * x.element_size() for x in xh))
+        out["d2h"] = int(lh.numel() * lh.element_size())
+    batch.close()
+    for p in plans:
+        p.close()
+    return out
+
+
+def ensemble_flops(insts):
+    return sum(i["N"] * flops_per_point(i["widths"], 4) for i in insts)
+
+
+def run_ensemble(args, rank, ws, local):
+    """The batched ensemble as the headline."""
+    form = args.form or "bf16"
+    W = max(args.warmup, 3)
     clocks = Clocks(local)
     barrier(ws)
     clocks.start()
-    evs = []
-    for _ in range(args.steps):
-        flush_buf.fill_(1.0)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        g.replay()
-        b.record()
-        evs.append((a, b))
-    torch.cuda.synchronize()
-    ms_local = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    # end to end: pinned host points in, losses out, every step
-    lh = torch.empty(len(insts), dtype=torch.float64).pin_memory()
-    evs = []
-    for _ in range(args.steps):
-        flush_buf.fill_(1.0)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        for xd, xp in zip(xs, xh):
-            xd.copy_(xp, non_blocking=True)
-        g.replay()
-        lh.copy_(loss, non_blocking=True)
-        b.record()
-        evs.append((a, b))
-    torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    res = time_ensemble(form, args.steps, W, rank)
     barrier(ws)
     clk = clocks.stop()
-    ms, value = aggregate(ms_local, n_pts, ws)
-    e2e_ms = max_over_ranks(e2e_ms, ws)
-    flops = sum(i["N"] * flops_per_point(i["widths"], 4) for i in insts)
+    insts = res["insts"]
+    ms, value = aggregate(res["ms_per_step"], res["n_pts"], ws)
+    e2e_ms = max_over_ranks(res["e2e_ms"], ws)
     peaks, peak_kind = measured_peaks()
-    roof = roofline(form, flops, ms_local, peaks, peak_kind, traffic_for("ensemble_64", form))
-    roof["kernel"] = "batched step (graph replay: weight preparation, persistent tcgen05 kernel, reduce + Adam)"
+    roof = roofline(form, ensemble_flops(insts), res["ms_per_step"], peaks, peak_kind,
+                    traffic_for("ensemble_64", form))
+    roof["kernel"] = "batched step (graph replay: weight preparation, persistent fused kernel, reduce + Adam)"
+    tune = res["tune"]
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": W,
            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "bf16x3": "bf16x3"}[form], "data": "synthetic",
-           "config": {"workload": "ensemble_64", "instances": len(insts), "points_per_replica": n_pts,
+           "dtype": DTYPES[form], "data": "synthetic",
+           "config": {"workload": "ensemble_64", "instances": len(insts), "points_per_replica": res["n_pts"],
                       "widths": sorted(set(i["widths"][1] for i in insts)),
                       "depths": [min(len(i["widths"]) - 2 for i in insts), max(len(i["widths"]) - 2 for i in insts)],
                       "form": form,
                       "tiles": "autotuned on the batch: %s CTA(s)/SM, %g x each shape's default tile (%s points); "
                                "options timed (ms): %s" % (tune.get("ctas"), tune.get("scale", 1.0),
-                                                          ",".join(str(t) for t in sorted(set(tiles))),
+                                                          ",".join(str(t) for t in sorted(set(res["tiles"]))),
                                                           tune.get("ms")),
                       "l2": "flushed between steps (2x L2 write, outside the per-step events)",
-                      "step": "jet_batch_train_step of all instances, one CUDA graph replay"},
-           "e2e": {"value": ws * n_pts / (e2e_ms * 1e-3), "unit": UNIT,
-                   "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in xh)),
-                   "d2h_bytes_per_step": int(lh.numel() * lh.element_size())},
-           "gpu_launches": 3 * args.steps, "roofline": roof, "clocks": clk, "cpu_baseline": None}
+                      "step": "jet_batch_train_step_dev of all instances, one CUDA graph replay"},
+           "e2e": {"value": ws * res["n_pts"] / (e2e_ms * 1e-3), "unit": UNIT,
+                   "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
+           "gpu_launches": launches_per_step(form, "tile", True, True) * args.steps, "roofline": roof,
+           "clocks": clk, "cpu_baseline": None}
     if rank == 0:
         print(json.dumps(out))
+
+
+def side_entry(name, form, schedule, steps, flush, peaks, peak_kind):
+    """One named workload timed beside the headline (rank 0, one replica)."""
+    from paper_2606_29702_gb300 import workloads as wl
+    if name == "ensemble_64":
+        r = time_ensemble(form, steps, 3, e2e=False)
+        return {"value": r["value"], "ms_per_step": r["ms_per_step"], "points": r["n_pts"], "form": form,
+                "step": "one CUDA graph replay of jet_batch_train_step_dev",
+                "roofline": dict(roofline(form, ensemble_flops(r["insts"]), r["ms_per_step"], peaks, peak_kind,
+                                          traffic_for(name, form)),
+                                 kernel="batched step (graph replay)")}
+    spec = dict(wl.WORKLOADS[name])
+    X = wl.points(spec["domain"], spec["N"], spec["seed_pts"])
+    r = time_form(spec, form, X, steps, 3, flush, want_kernel=True, schedule=schedule)
+    fpp = flops_per_point(spec["widths"], r["info"]["n_channels"])
+    return {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernel_ms": r["kernel_ms"], "points": spec["N"],
+            "form": form, "schedule": schedule, "tile_points": r["info"]["tile_points"],
+            "grid_ctas": r["info"]["grid_ctas"], "channels": r["info"]["n_channels"],
+            "roofline": roofline(form, fpp * spec["N"], r["kernel_ms"], peaks, peak_kind,
+                                 traffic_for(name, form, schedule))}
 
 
 def run_ours(args, rank, ws, local):
@@ -512,18 +597,21 @@ def run_ours(args, rank, ws, local):
     if args.n:
         spec["N"] = args.n
     form = args.form or spec["precision"]
+    schedule = args.schedule or default_schedule(spec, form)
     X = wl.points(spec["domain"], spec["N"], spec["seed_pts"] + rank)
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def flush():
         flush_buf.fill_(1.0)
 
-    # warm-up compile / first launch outside the timed region
+    if args.train:
+        return run_train(args, spec, form, schedule, X, rank, ws, local)
     clocks = Clocks(local)
     barrier(ws)
     torch.cuda.synchronize()
     clocks.start()
-    res = time_form(spec, form, X, args.steps, max(args.warmup, 3), flush, want_kernel=True, e2e=True)
+    res = time_form(spec, form, X, args.steps, max(args.warmup, 3), flush, want_kernel=True, e2e=True,
+                    schedule=schedule)
     torch.cuda.synchronize()
     barrier(ws)
     clk = clocks.stop()
@@ -531,37 +619,88 @@ def run_ours(args, rank, ws, local):
     C = res["info"]["n_channels"]
     fpp = flops_per_point(spec["widths"], C)
     peaks, peak_kind = measured_peaks()
-    roof = roofline(form, fpp * spec["N"], res["kernel_ms"], peaks, peak_kind, traffic_for(args.workload, form))
-    forms = {}
+    roof = roofline(form, fpp * spec["N"], res["kernel_ms"], peaks, peak_kind,
+                    traffic_for(args.workload, form, schedule))
+    if schedule == "store":
+        roof["kernel"] += " + store weight-gradient GEMM"
+    side = {}
     if not args.no_forms and rank == 0:
-        for f in ("fp32", "bf16", "bf16x3", "tf32", "fp64"):
-            if f == form:
+        for name, f, sc in SIDE:
+            if (name, f, sc) == (args.workload, form, schedule):
                 continue
+            key = "%s/%s/%s" % (name, f, sc)
             try:
-                r = time_form(spec, f, X, max(3, args.steps // 2), 3, flush, want_kernel=True)
-                forms[f] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernel_ms": r["kernel_ms"],
-                            "tile_points": r["info"]["tile_points"], "grid_ctas": r["info"]["grid_ctas"],
-                            "roofline": roofline(f, fpp * spec["N"], r["kernel_ms"], peaks, peak_kind,
-                                                 traffic_for(args.workload, f))}
+                side[key] = side_entry(name, f, sc, max(3, args.steps // 2), flush, peaks, peak_kind)
             except Exception as e:  # a form this build does not provide
-                forms[f] = {"unavailable": str(e).splitlines()[0][:160]}
+                side[key] = {"unavailable": str(e).splitlines()[0][:160]}
+            torch.cuda.empty_cache()
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "tf32": "tf32",
-                                          "bf16x3": "bf16x3"}[form],
-           "data": "synthetic",
+           "vs_baseline": None, "dtype": DTYPES[form], "data": "synthetic",
            "config": {"workload": args.workload, "N": spec["N"], "widths": spec["widths"], "form": form,
-                      "channels": C, "l2": "flushed between steps (2x L2 write, outside the per-step events)",
+                      "schedule": schedule, "channels": C, "tile_points": res["info"]["tile_points"],
+                      "l2": "flushed between steps (2x L2 write, outside the per-step events)",
                       "step": "jet_train_step: forward jets + residual + loss + reverse sweep + FP64 reduce + Adam"},
-           "e2e": res["e2e"], "gpu_launches": 3 * args.steps, "roofline": roof, "clocks": clk,
-           "forms": forms}
+           "e2e": res["e2e"], "gpu_launches": launches_per_step(form, schedule) * args.steps, "roofline": roof,
+           "clocks": clk, "workloads": side}
     if rank == 0:
         if ws == 1 and args.cpu_seconds > 0:
-            out["cpu_baseline"], out["rel_err_vs_fp64"] = cpu_baseline(
-                spec, args.cpu_seconds, [form] + [f for f in forms if "unavailable" not in forms[f]])
+            forms = [form] + sorted({f for n, f, _ in SIDE if n == args.workload and f != form})
+            out["cpu_baseline"], out["rel_err_vs_fp64"] = cpu_baseline(spec, args.cpu_seconds, forms)
         else:
             out["cpu_baseline"] = None
         print(json.dumps(out))
+
+
+def run_train(args, spec, form, schedule, X, rank, ws, local):
+    """K Adam steps (lr 1e-3) after 20 warm-up steps on a fresh initialisation,
+    with the loss of every step kept on the device (Sec. 3.1.1 protocol: 1000
+    steps, 20 warm-up steps, CUDA events around the steps)."""
+    import torch
+    from paper_2606_29702_gb300 import specs
+    from paper_2606_29702_gb300 import workloads as wl
+    sp, plan = make_plan(spec, form, schedule)
+    dt = plan.dtype
+    dev = torch.device("cuda")
+    p0 = torch.tensor(wl.pack(wl.xavier_layers(spec["widths"], spec["seed_par"])), dtype=dt, device=dev)
+    x = torch.tensor(X, dtype=dt, device=dev)
+    src = torch.tensor(specs.helmholtz_source(X, spec["coefs"]["k"]), dtype=dt, device=dev) if sp.has_source \
+        else None
+    K, W = args.train, 20
+    # warm-up on a scratch copy, so that the timed run starts at step 1
+    pw, mw, vw = p0.clone(), torch.zeros_like(p0), torch.zeros_like(p0)
+    cw = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(W):
+        plan.train_step_dev(pw, mw, vw, cw, 1e-3, x, src)
+    p, m, v = p0.clone(), torch.zeros_like(p0), torch.zeros_like(p0)
+    ctr = torch.zeros(1, dtype=torch.int64, device=dev)
+    hist = torch.empty(K, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for k in range(K):
+        plan.train_step_dev(p, m, v, ctr, 1e-3, x, src, loss=hist[k])
+    b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b) / K
+    h = hist.cpu().numpy()
+    out = {"metric": METRIC, "value": spec["N"] / (ms * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+           "ms_per_step": ms, "total_s": ms * K / 1e3, "dtype": DTYPES[form], "data": "synthetic",
+           "config": {"workload": args.workload, "N": spec["N"], "widths": spec["widths"], "form": form,
+                      "schedule": schedule, "lr": 1e-3, "adam_steps": int(ctr.item()),
+                      "step": "jet_train_step_dev, one call per step, no L2 flush between steps"},
+           "loss_first": float(h[0]), "loss_last": float(h[-1]),
+           "loss_every_50": [float(h[i]) for i in range(0, K, 50)] + [float(h[-1])], "clocks": clk}
+    if args.history:
+        with open(args.history, "w") as f:
+            json.dump({"loss": h.tolist(), **{k: out[k] for k in ("config", "ms_per_step")}}, f)
+    if rank == 0:
+        print(json.dumps(out))
+    plan.close()
 
 
 def main():

@@ -65,7 +65,8 @@ typedef enum {
 typedef enum {
   JET_FP64 = 0,     /* FP64 SIMT kernels */
   JET_FP32 = 1,     /* plain FP32 SIMT kernels (no tensor cores) */
-  JET_TF32 = 2,     /* tcgen05 kind::tf32 jet GEMMs, FP32 accumulation */
+  JET_TF32 = 2,     /* reserved: not provided by this build (jet_plan_create
+                       returns JET_ERR_UNSUPPORTED) */
   JET_BF16 = 3,     /* tcgen05 kind::f16 (bf16) jet GEMMs, FP32 accumulation */
   JET_BF16X3 = 4    /* as JET_BF16, plus split bf16 hi/lo products on the
                        highest-order channels (hidden width <= 128) */
@@ -199,10 +200,29 @@ jet_status jet_backward_params(jet_plan_t plan, const void* params, const void* 
  *   adam_m, adam_v  device, packed like params, value type of the plan;
  *                   zero before step 1.
  *   loss_out        device double or NULL: the loss BEFORE the update.
- * Not available for JET_FP64 plans' mixed forms: any precision works.
+ * Works for every plan precision; the update runs in the parameters' value
+ * type (FP64 for JET_FP64, FP32 otherwise).  `step` is a host value: a CUDA
+ * graph that captures this call repeats that step's bias correction on every
+ * replay.  Use jet_train_step_dev for replayed training loops.
  */
 jet_status jet_train_step(jet_plan_t plan, void* params, void* adam_m, void* adam_v, int64_t step, float lr,
                           const void* X, int64_t N, const void* source, double* loss_out, jet_stream_t stream);
+
+/*
+ * jet_train_step with the Adam step counter in device memory (Sec. 3.1.1,
+ * full-batch Adam).
+ *   step_counter  device int64: the number of Adam steps already taken
+ *                 (0 before the first).  The call performs step
+ *                 t = *step_counter + 1 (bias corrections 1 - beta^t computed
+ *                 on the device) and then increments *step_counter on the
+ *                 stream, so k launches of the same captured CUDA graph take
+ *                 k consecutive Adam steps.
+ * Everything else as jet_train_step; both calls give identical results for
+ * the same step number.
+ */
+jet_status jet_train_step_dev(jet_plan_t plan, void* params, void* adam_m, void* adam_v, int64_t* step_counter,
+                              float lr, const void* X, int64_t N, const void* source, double* loss_out,
+                              jet_stream_t stream);
 
 jet_status jet_plan_destroy(jet_plan_t plan);
 
@@ -220,6 +240,13 @@ jet_status jet_batch_train_step(jet_batch_t batch, void* const* params, void* co
                                 void* const* adam_v, int64_t step, float lr, const void* const* X,
                                 const int64_t* N, const void* const* source,
                                 double* loss_out /* device [n] or NULL */, jet_stream_t stream);
+/* As jet_batch_train_step, with one device step counter shared by every
+ * instance (see jet_train_step_dev): all instances take step
+ * t = *step_counter + 1, then the counter is incremented on the stream. */
+jet_status jet_batch_train_step_dev(jet_batch_t batch, void* const* params, void* const* adam_m,
+                                    void* const* adam_v, int64_t* step_counter, float lr, const void* const* X,
+                                    const int64_t* N, const void* const* source,
+                                    double* loss_out /* device [n] or NULL */, jet_stream_t stream);
 jet_status jet_batch_destroy(jet_batch_t batch);
 
 /*
@@ -248,10 +275,10 @@ jet_status jet_plan_profile_read(jet_plan_t plan, int64_t* launches, double* tot
  * jet_backward_params without any device allocation (the paper has no
  * counterpart: this is a deployment convenience of this library).
  *
- * For callers that cannot call cudaMalloc -- code recording a CUDA graph
- * against its own memory pools, runtimes that own every device allocation,
- * or loops that forbid allocator calls after start-up -- and therefore cannot
- * create a plan.  It takes the jet_plan_create arguments (JET_FP64 or
+ * For callers that cannot call cudaMalloc -- runtimes that own every device
+ * allocation themselves, or real-time loops that forbid allocator calls after
+ * start-up -- and therefore cannot create a plan (jet_plan_create allocates
+ * the plan's workspace).  It takes the jet_plan_create arguments (JET_FP64 or
  * JET_FP32 only) together with the jet_backward_params arguments, and keeps
  * all working memory (weight copies, per-chunk FP64 gradient slices,
  * per-CTA jet scratch) in one file-scope device array of 8 MiB that every
@@ -265,8 +292,8 @@ jet_status jet_plan_profile_read(jet_plan_t plan, int64_t* launches, double* tot
  * with cudaGetSymbolAddress (that device current); make that first call
  * before any stream capture.  Every call reuses the same array and leaves its
  * contents behind; each call writes every part it reads, so nothing has to be
- * cleared, but calls that overlap on the GPU (two streams, two threads, two
- * graph replays in flight) race on the array and must be serialised.
+ * cleared, but calls that overlap on the GPU (two streams or two host
+ * threads) race on the array and must be serialised by the caller.
  */
 jet_status jet_backward_params_noalloc(const jet_residual_spec* spec, int32_t d_in, int32_t n_layers,
                                        const int32_t* widths, int32_t n_needed, const jet_chan* needed,

@@ -556,16 +556,18 @@ jet_status jet_backward_params(jet_plan_t p, const void* params, const void* X, 
   return JET_OK;
 }
 
-jet_status jet_train_step(jet_plan_t p, void* params, void* adam_m, void* adam_v, int64_t step, float lr,
-                          const void* X, int64_t N, const void* source, double* loss_out, jet_stream_t stream) {
+}  // extern "C"
+
+// Adam step t = `step`, or *step_ctr + 1 (then incremented) with a device counter
+static jet_status train_step(jet_plan_t p, void* params, void* adam_m, void* adam_v, int64_t step,
+                             long long* step_ctr, float lr, const void* X, int64_t N, const void* source,
+                             double* loss_out, cudaStream_t s) {
   jet_status st = check_call(p, params, X, N, source);
   if (st != JET_OK) return st;
   if (!adam_m || !adam_v) return fail(JET_ERR_INVALID, "NULL Adam state");
-  if (step < 1) return fail(JET_ERR_INVALID, "step must be >= 1");
   if (N < 1) return fail(JET_ERR_INVALID, "train step needs N >= 1");
-  cudaStream_t s = (cudaStream_t)stream;
   p->st_valid = false;  // params change in place
-  if (p->tc) return tc_train_step(p, p->tcp, params, adam_m, adam_v, step, lr, X, N, source, loss_out, s);
+  if (p->tc) return tc_train_step(p, p->tcp, params, adam_m, adam_v, step, step_ctr, lr, X, N, source, loss_out, s);
   DevInstance I;
   fill_instance(p, params, X, N, source, nullptr, p->grid, I);
   CK(launch_transpose_weights(I, p->fp64, p->Wt, s));
@@ -575,8 +577,24 @@ jet_status jet_train_step(jet_plan_t p, void* params, void* adam_m, void* adam_v
   j.params = params;
   j.m = adam_m;
   j.v = adam_v;
-  CK(launch_reduce(nullptr, j, 1, I.n_params, p->fp64, true, step, lr, s));
+  CK(launch_reduce(nullptr, j, 1, I.n_params, p->fp64, true, step, lr, s, step_ctr));
   return JET_OK;
+}
+
+extern "C" {
+
+jet_status jet_train_step(jet_plan_t p, void* params, void* adam_m, void* adam_v, int64_t step, float lr,
+                          const void* X, int64_t N, const void* source, double* loss_out, jet_stream_t stream) {
+  if (step < 1) return fail(JET_ERR_INVALID, "step must be >= 1");
+  return train_step(p, params, adam_m, adam_v, step, nullptr, lr, X, N, source, loss_out, (cudaStream_t)stream);
+}
+
+jet_status jet_train_step_dev(jet_plan_t p, void* params, void* adam_m, void* adam_v, int64_t* step_counter,
+                              float lr, const void* X, int64_t N, const void* source, double* loss_out,
+                              jet_stream_t stream) {
+  if (!step_counter) return fail(JET_ERR_INVALID, "NULL step counter");
+  return train_step(p, params, adam_m, adam_v, 1, reinterpret_cast<long long*>(step_counter), lr, X, N, source,
+                    loss_out, (cudaStream_t)stream);
 }
 
 jet_status jet_debug_activation(jet_plan_t p, int32_t kind, int64_t n, const double* z, const double* v, double* out,
@@ -768,7 +786,7 @@ jet_status jet_batch_create(jet_batch_t* out, int32_t n, const jet_plan_t* plans
 }
 
 static jet_status batch_run(jet_batch_t b, const void* const* params, void* const* adam_m, void* const* adam_v,
-                            int64_t step, float lr, const void* const* X, const int64_t* N,
+                            int64_t step, long long* step_ctr, float lr, const void* const* X, const int64_t* N,
                             const void* const* source, void* const* grad_out, double* loss_out, bool adam,
                             cudaStream_t s) {
   const int n = (int)b->plans.size();
@@ -805,7 +823,7 @@ static jet_status batch_run(jet_batch_t b, const void* const* params, void* cons
     CK(cudaEventRecord(b->copied, s));
     b->have_prev = true;
   }
-  CK(launch_reduce(b->d_jobs, b->h_jobs[0], n, maxp, b->fp64, adam, step, lr, s));
+  CK(launch_reduce(b->d_jobs, b->h_jobs[0], n, maxp, b->fp64, adam, step, lr, s, step_ctr));
   return JET_OK;
 }
 
@@ -813,21 +831,35 @@ jet_status jet_batch_backward(jet_batch_t b, const void* const* params, const vo
                               const void* const* source, void* const* grad_out, double* loss_out,
                               jet_stream_t stream) {
   if (!b || !params || !X || !N || !grad_out) return fail(JET_ERR_INVALID, "NULL batch argument");
-  if (b->tc) return tc_batch_run(b->tcb, b->plans, params, nullptr, nullptr, 0, 0.f, X, N, source, grad_out,
-                                 loss_out, false, (cudaStream_t)stream);
-  return batch_run(b, params, nullptr, nullptr, 0, 0.f, X, N, source, grad_out, loss_out, false,
+  if (b->tc) return tc_batch_run(b->tcb, b->plans, params, nullptr, nullptr, 0, nullptr, 0.f, X, N, source,
+                                 grad_out, loss_out, false, (cudaStream_t)stream);
+  return batch_run(b, params, nullptr, nullptr, 0, nullptr, 0.f, X, N, source, grad_out, loss_out, false,
                    (cudaStream_t)stream);
+}
+
+static jet_status batch_train(jet_batch_t b, void* const* params, void* const* adam_m, void* const* adam_v,
+                              int64_t step, long long* step_ctr, float lr, const void* const* X, const int64_t* N,
+                              const void* const* source, double* loss_out, cudaStream_t s) {
+  if (!b || !params || !adam_m || !adam_v || !X || !N) return fail(JET_ERR_INVALID, "NULL batch argument");
+  if (b->tc) return tc_batch_run(b->tcb, b->plans, (const void* const*)params, adam_m, adam_v, step, step_ctr, lr,
+                                 X, N, source, nullptr, loss_out, true, s);
+  return batch_run(b, (const void* const*)params, adam_m, adam_v, step, step_ctr, lr, X, N, source, nullptr,
+                   loss_out, true, s);
 }
 
 jet_status jet_batch_train_step(jet_batch_t b, void* const* params, void* const* adam_m, void* const* adam_v,
                                 int64_t step, float lr, const void* const* X, const int64_t* N,
                                 const void* const* source, double* loss_out, jet_stream_t stream) {
-  if (!b || !params || !adam_m || !adam_v || !X || !N) return fail(JET_ERR_INVALID, "NULL batch argument");
   if (step < 1) return fail(JET_ERR_INVALID, "step must be >= 1");
-  if (b->tc) return tc_batch_run(b->tcb, b->plans, (const void* const*)params, adam_m, adam_v, step, lr, X, N,
-                                 source, nullptr, loss_out, true, (cudaStream_t)stream);
-  return batch_run(b, (const void* const*)params, adam_m, adam_v, step, lr, X, N, source, nullptr, loss_out, true,
-                   (cudaStream_t)stream);
+  return batch_train(b, params, adam_m, adam_v, step, nullptr, lr, X, N, source, loss_out, (cudaStream_t)stream);
+}
+
+jet_status jet_batch_train_step_dev(jet_batch_t b, void* const* params, void* const* adam_m, void* const* adam_v,
+                                    int64_t* step_counter, float lr, const void* const* X, const int64_t* N,
+                                    const void* const* source, double* loss_out, jet_stream_t stream) {
+  if (!step_counter) return fail(JET_ERR_INVALID, "NULL step counter");
+  return batch_train(b, params, adam_m, adam_v, 1, reinterpret_cast<long long*>(step_counter), lr, X, N, source,
+                     loss_out, (cudaStream_t)stream);
 }
 
 jet_status jet_batch_destroy(jet_batch_t b) {

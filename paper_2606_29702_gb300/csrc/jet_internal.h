@@ -130,9 +130,11 @@ struct ReduceJob {
   void* v;
 };
 cudaError_t launch_transpose_weights(const DevInstance& in, bool fp64, void* Wt, cudaStream_t s);
-// jobs: host array copied by value when n == 1, else a device array
+// jobs: host array copied by value when n == 1, else a device array.  Adam
+// takes step t = `step`, or *step_ctr + 1 with a device counter, which the
+// call then increments on the stream.
 cudaError_t launch_reduce(const ReduceJob* dev_jobs, const ReduceJob& job0, int n, long long max_params, bool fp64,
-                          bool adam, long long step, float lr, cudaStream_t s);
+                          bool adam, long long step, float lr, cudaStream_t s, long long* step_ctr = nullptr);
 
 }  // namespace jet
 

@@ -1,10 +1,9 @@
 // jet_backward_params_noalloc: the parameter gradient of the fused SIMT kernel
 // without any device allocation.
 //
-// Who needs it: code that must not call cudaMalloc -- for example a caller
-// that is recording a CUDA graph with its own memory pools, an embedding
-// runtime that owns every device allocation itself, or a real-time loop that
-// forbids allocator calls after start-up.  Such callers cannot create a plan
+// Who needs it: code that must not call cudaMalloc -- for example an
+// embedding runtime that owns every device allocation itself, or a real-time
+// loop that forbids allocator calls after start-up.  Such callers cannot create a plan
 // (jet_plan_create allocates the plan's workspace), so this entry point takes
 // the plan arguments and the call arguments together and keeps all of its
 // working memory in one file-scope device array of fixed size.
@@ -133,6 +132,14 @@ extern "C" jet_status jet_backward_params_noalloc(const jet_residual_spec* spec,
   if (spec->n_res < 1 || spec->n_res > kMaxRes || !spec->n_mono || !spec->mono)
     return nfail(JET_ERR_INVALID, "residual spec");
   if ((spec->has_source != 0) != (source != nullptr)) return nfail(JET_ERR_INVALID, "source does not match spec");
+  // the same spec and multi-index checks as jet_plan_create, before anything
+  // below dereferences the monomial lists
+  for (int c = 0; c < spec->n_res; ++c)
+    if (spec->n_mono[c] < 0 || (spec->n_mono[c] > 0 && !spec->mono[c]))
+      return nfail(JET_ERR_INVALID, "residual component with a bad monomial list");
+  for (int i = 0; i < n_needed; ++i)
+    for (int j = d_in; j < 4; ++j)
+      if (needed[i].alpha[j]) return nfail(JET_ERR_INVALID, "a needed multi-index differentiates a coordinate >= d_in");
   // smallest compiled channel set containing every needed multi-index and
   // every multi-index below them (checked componentwise, no heap)
   int best = -1;
@@ -181,6 +188,8 @@ extern "C" jet_status jet_backward_params_noalloc(const jet_residual_spec* spec,
       t.comp = c;
       t.nfac = mo.n_fac;
       for (int f = 0; f < mo.n_fac; ++f) {
+        for (int j = d_in; j < 4; ++j)
+          if (mo.fac[f].alpha[j]) return nfail(JET_ERR_INVALID, "a residual factor differentiates a coordinate >= d_in");
         const int ch = chan_of(ci, d_in, mo.fac[f].alpha);
         if (ch < 0 || mo.fac[f].out < 0 || mo.fac[f].out >= n_out)
           return nfail(JET_ERR_INVALID, "residual factor outside the carried channels");

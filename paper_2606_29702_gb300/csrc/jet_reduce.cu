@@ -37,9 +37,14 @@ cudaError_t launch_transpose_weights(const DevInstance& in, bool fp64, void* Wt,
 // paper fixes only the learning rate (1e-3).  The update runs in the value
 // type of the parameters (FP32 for the FP32 and BF16 forms); the gradient it
 // takes is the FP64 sum over chunks.
+// The 1-based step t is `step`, or *step_ctr + 1 when the counter lives in
+// device memory; the bias corrections 1 - beta^t are formed on the device in
+// both cases, so the two give identical updates for the same t.
 struct AdamConst {
-  double lr, beta1, beta2, eps, bc1, bc2;
-  float lr_f, beta1_f, beta2_f, eps_f, bc1_f, bc2_f;
+  double lr, beta1, beta2, eps;
+  float lr_f, beta1_f, beta2_f, eps_f;
+  long long step;
+  const long long* step_ctr;
 };
 
 // One block takes 32 consecutive parameters (lanes over parameters, so every
@@ -55,6 +60,13 @@ __global__ void __launch_bounds__(32 * kRedWarps) reduce_kernel(const __grid_con
   __shared__ double part[kRedWarps][32];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int gc = J.grad_chunks > 0 ? J.grad_chunks : J.n_chunks;
+  double bc1 = 1.0, bc2 = 1.0;
+  if (ADAM) {
+    const long long t = ac.step_ctr ? *ac.step_ctr + 1 : ac.step;
+    bc1 = 1.0 - pow(ac.beta1, (double)t);
+    bc2 = 1.0 - pow(ac.beta2, (double)t);
+  }
+  const float bc1_f = (float)bc1, bc2_f = (float)bc2;
   for (long long p0 = (long long)blockIdx.x * 32; p0 < J.n_params; p0 += (long long)gridDim.x * 32) {
     const long long p = p0 + lane;
     double g = 0.0;
@@ -77,13 +89,13 @@ __global__ void __launch_bounds__(32 * kRedWarps) reduce_kernel(const __grid_con
           const float vv = ac.beta2_f * v[p] + (1.0f - ac.beta2_f) * gf * gf;
           m[p] = mm;
           v[p] = vv;
-          th[p] = th[p] - ac.lr_f * (mm / ac.bc1_f) / (sqrtf(vv / ac.bc2_f) + ac.eps_f);
+          th[p] = th[p] - ac.lr_f * (mm / bc1_f) / (sqrtf(vv / bc2_f) + ac.eps_f);
         } else {
           const double mm = ac.beta1 * (double)m[p] + (1.0 - ac.beta1) * g;
           const double vv = ac.beta2 * (double)v[p] + (1.0 - ac.beta2) * g * g;
           m[p] = (T)mm;
           v[p] = (T)vv;
-          const double mhat = mm / ac.bc1, vhat = vv / ac.bc2;
+          const double mhat = mm / bc1, vhat = vv / bc2;
           th[p] = (T)((double)th[p] - ac.lr * mhat / (sqrt(vhat) + ac.eps));
         }
       }
@@ -97,21 +109,22 @@ __global__ void __launch_bounds__(32 * kRedWarps) reduce_kernel(const __grid_con
   }
 }
 
+// the device step counter advances once the update that read it is done
+__global__ void adam_advance_kernel(long long* step_ctr) { *step_ctr += 1; }
+
 cudaError_t launch_reduce(const ReduceJob* dev_jobs, const ReduceJob& job0, int n, long long max_params, bool fp64,
-                          bool adam, long long step, float lr, cudaStream_t s) {
+                          bool adam, long long step, float lr, cudaStream_t s, long long* step_ctr) {
   AdamConst ac;
   ac.lr = lr;
   ac.beta1 = 0.9;
   ac.beta2 = 0.999;
   ac.eps = 1e-8;
-  ac.bc1 = 1.0 - pow(ac.beta1, (double)(step < 1 ? 1 : step));
-  ac.bc2 = 1.0 - pow(ac.beta2, (double)(step < 1 ? 1 : step));
   ac.lr_f = lr;
   ac.beta1_f = 0.9f;
   ac.beta2_f = 0.999f;
   ac.eps_f = 1e-8f;
-  ac.bc1_f = (float)ac.bc1;
-  ac.bc2_f = (float)ac.bc2;
+  ac.step = step < 1 ? 1 : step;
+  ac.step_ctr = adam ? step_ctr : nullptr;
   long long gx = (max_params + 31) / 32;
   if (gx > 4096) gx = 4096;
   if (gx < 1) gx = 1;
@@ -124,6 +137,11 @@ cudaError_t launch_reduce(const ReduceJob* dev_jobs, const ReduceJob& job0, int 
   } else {
     if (adam) reduce_kernel<float, true><<<grid, threads, 0, s>>>(job0, jobs, ac);
     else reduce_kernel<float, false><<<grid, threads, 0, s>>>(job0, jobs, ac);
+  }
+  if (adam && step_ctr) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    adam_advance_kernel<<<1, 1, 0, s>>>(step_ctr);
   }
   return cudaGetLastError();
 }

@@ -882,8 +882,9 @@ jet_status tc_backward(jet_plan_s* p, TcPlan* t, const void* params, const void*
   return e == cudaSuccess ? JET_OK : tcuda(e, "reduce");
 }
 
-jet_status tc_train_step(jet_plan_s* p, TcPlan* t, void* params, void* m, void* v, long long step, float lr,
-                         const void* X, long long N, const void* source, double* loss_out, cudaStream_t s) {
+jet_status tc_train_step(jet_plan_s* p, TcPlan* t, void* params, void* m, void* v, long long step,
+                         long long* step_ctr, float lr, const void* X, long long N, const void* source,
+                         double* loss_out, cudaStream_t s) {
   jet_status st = check_err(t);
   if (st != JET_OK) return st;
   ensure_store(t, N);
@@ -906,7 +907,7 @@ jet_status tc_train_step(jet_plan_s* p, TcPlan* t, void* params, void* m, void* 
   j.params = params;
   j.m = m;
   j.v = v;
-  cudaError_t e = launch_reduce(nullptr, j, 1, p->n_params, false, true, step, lr, s);
+  cudaError_t e = launch_reduce(nullptr, j, 1, p->n_params, false, true, step, lr, s, step_ctr);
   return e == cudaSuccess ? JET_OK : tcuda(e, "reduce/adam");
 }
 
@@ -1015,7 +1016,8 @@ void tc_batch_destroy(TcBatch* b) {
 }
 
 jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, const void* const* params, void* const* m,
-                        void* const* v, long long step, float lr, const void* const* X, const int64_t* N,
+                        void* const* v, long long step, long long* step_ctr, float lr, const void* const* X,
+                        const int64_t* N,
                         const void* const* source, void* const* grad_out, double* loss_out, bool adam,
                         cudaStream_t s) {
   TcBatch* b = bb;
@@ -1140,7 +1142,7 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
     if (e == cudaSuccess && !capturing) e = cudaEventRecord(b->copied, s);
     if (e != cudaSuccess) return tcuda(e, "batch job upload");
   }
-  e = launch_reduce(b->d_jobs, b->h_jobs[0], n, maxp, false, adam, step, lr, s);
+  e = launch_reduce(b->d_jobs, b->h_jobs[0], n, maxp, false, adam, step, lr, s, step_ctr);
   return e == cudaSuccess ? JET_OK : tcuda(e, "batch reduce");
 }
 

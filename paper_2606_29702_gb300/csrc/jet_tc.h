@@ -27,11 +27,13 @@ jet_status tc_forward(jet_plan_s* p, jet::TcPlan* t, const void* params, const v
                       const void* source, void* r_out, double* loss_out, cudaStream_t s);
 jet_status tc_backward(jet_plan_s* p, jet::TcPlan* t, const void* params, const void* X, long long N,
                        const void* source, void* grad_out, void* r_out, double* loss_out, cudaStream_t s);
-jet_status tc_train_step(jet_plan_s* p, jet::TcPlan* t, void* params, void* m, void* v, long long step, float lr,
-                         const void* X, long long N, const void* source, double* loss_out, cudaStream_t s);
+jet_status tc_train_step(jet_plan_s* p, jet::TcPlan* t, void* params, void* m, void* v, long long step,
+                         long long* step_ctr, float lr, const void* X, long long N, const void* source,
+                         double* loss_out, cudaStream_t s);
 jet_status tc_batch_create(const std::vector<jet_plan_s*>& plans, jet::TcBatch** out);
 void tc_batch_destroy(jet::TcBatch* b);
 jet_status tc_batch_run(jet::TcBatch* b, const std::vector<jet_plan_s*>& plans, const void* const* params,
-                        void* const* m, void* const* v, long long step, float lr, const void* const* X,
+                        void* const* m, void* const* v, long long step, long long* step_ctr, float lr,
+                        const void* const* X,
                         const int64_t* N, const void* const* source, void* const* grad_out, double* loss_out,
                         bool adam, cudaStream_t s);

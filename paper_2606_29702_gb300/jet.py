@@ -53,7 +53,8 @@ class JetPlanInfo(ctypes.Structure):
 
 
 EXPORTS = ["jet_plan_create", "jet_plan_get_info", "jet_forward_residual", "jet_backward_params", "jet_train_step",
-           "jet_plan_destroy", "jet_batch_create", "jet_batch_backward", "jet_batch_train_step", "jet_batch_destroy",
+           "jet_train_step_dev", "jet_plan_destroy", "jet_batch_create", "jet_batch_backward", "jet_batch_train_step",
+           "jet_batch_train_step_dev", "jet_batch_destroy",
            "jet_debug_activation", "jet_plan_profile", "jet_plan_profile_read", "jet_backward_params_noalloc",
            "jet_debug_wait_timeout", "jet_last_error", "jet_version"]
 
@@ -75,6 +76,7 @@ def load():
     L.jet_forward_residual.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
     L.jet_backward_params.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp]
     L.jet_train_step.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, vp, i64, vp, vp, vp]
+    L.jet_train_step_dev.argtypes = [vp, vp, vp, vp, vp, ctypes.c_float, vp, i64, vp, vp, vp]
     L.jet_plan_destroy.argtypes = [vp]
     L.jet_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i32]
     L.jet_batch_backward.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i64),
@@ -82,6 +84,9 @@ def load():
     L.jet_batch_train_step.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i64,
                                        ctypes.c_float, ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(vp),
                                        vp, vp]
+    L.jet_batch_train_step_dev.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp,
+                                           ctypes.c_float, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                                           ctypes.POINTER(vp), vp, vp]
     L.jet_batch_destroy.argtypes = [vp]
     L.jet_debug_activation.argtypes = [vp, i32, i64, vp, vp, vp, vp]
     L.jet_backward_params_noalloc.argtypes = [ctypes.POINTER(JetResidualSpec), i32, i32, ctypes.POINTER(i32), i32,
@@ -222,6 +227,21 @@ class Plan:
                                      _ptr(source), _ptr(loss), _stream(stream)))
         return loss
 
+    def train_step_dev(self, params, m, v, step_counter, lr, X, source=None, loss=None, stream=None):
+        """In-place Adam step with a device step counter (jet_train_step_dev):
+        ``step_counter`` is a CUDA int64 tensor holding the steps already
+        taken; the call advances it on the device."""
+        N = X.shape[0]
+        for t, nme in ((params, "params"), (m, "adam_m"), (v, "adam_v")):
+            self._chk(t, nme)
+        self._chk(X, "X", (N, self.spec.d_in))
+        _chk_counter(step_counter)
+        if loss is None:
+            loss = torch.empty((), dtype=torch.float64, device=X.device)
+        _check(load().jet_train_step_dev(self._h, _ptr(params), _ptr(m), _ptr(v), _ptr(step_counter), float(lr),
+                                         _ptr(X), N, _ptr(source), _ptr(loss), _stream(stream)))
+        return loss
+
     def debug_activation(self, kind, z, v=None, stream=None):
         out = torch.empty_like(z)
         _check(load().jet_debug_activation(self._h, int(kind), z.shape[0], _ptr(z), _ptr(v), _ptr(out),
@@ -248,6 +268,11 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _chk_counter(t):
+    if not t.is_cuda or t.dtype != torch.int64 or t.numel() != 1:
+        raise ValueError("step_counter must be a one-element CUDA int64 tensor")
 
 
 def _vp_array(ts):
@@ -282,6 +307,19 @@ class Batch:
         src = _vp_array(sources) if sources is not None else None
         _check(load().jet_batch_train_step(self._h, _vp_array(params), _vp_array(m), _vp_array(v), int(step),
                                            float(lr), _vp_array(X), Ns, src, _ptr(loss), _stream(stream)))
+        return loss
+
+    def train_step_dev(self, params, m, v, step_counter, lr, X, sources=None, loss=None, stream=None):
+        """Batched Adam step with one device step counter (jet_batch_train_step_dev)."""
+        n = len(self.plans)
+        _chk_counter(step_counter)
+        if loss is None:
+            loss = torch.empty(n, dtype=torch.float64, device=X[0].device)
+        Ns = (ctypes.c_int64 * n)(*[x.shape[0] for x in X])
+        src = _vp_array(sources) if sources is not None else None
+        _check(load().jet_batch_train_step_dev(self._h, _vp_array(params), _vp_array(m), _vp_array(v),
+                                               _ptr(step_counter), float(lr), _vp_array(X), Ns, src, _ptr(loss),
+                                               _stream(stream)))
         return loss
 
     def close(self):

@@ -72,3 +72,42 @@ def test_unsupported_closure():
     sp = specs.Spec("x5", 2, 1, [[(1.0, [(0, (5, 0))])]])
     st, msg = _create(sp, [2, 16, 1], auto_close=True)
     assert st == 3
+
+
+def _noalloc_status(spec_struct, d_in, widths, needed):
+    """Status of jet_backward_params_noalloc for a spec the host checks must
+    reject: the pointers are never dereferenced and no CUDA call is made."""
+    lib = jet.load()
+    nd = (jet.JetChan * max(1, len(needed)))()
+    for i, al in enumerate(needed):
+        for j, k in enumerate(al):
+            nd[i].alpha[j] = k
+    w = (ctypes.c_int32 * len(widths))(*widths)
+    fake = ctypes.c_void_p(256)
+    st = lib.jet_backward_params_noalloc(ctypes.byref(spec_struct), d_in, len(widths) - 1, w, len(needed), nd,
+                                         jet.PRECISIONS["fp32"], fake, fake, 100, None, fake, None, None, None)
+    return st, lib.jet_last_error().decode()
+
+
+def test_noalloc_rejects_malformed_specs_on_the_host():
+    sp = specs.burgers(0.01)
+    needed = sp.closure()
+    # a negative monomial count
+    s, keep = jet._spec_struct(sp)
+    s.n_mono[0] = -1
+    st, msg = _noalloc_status(s, 2, [2, 20, 1], needed)
+    assert st == 1 and "monomial list" in msg
+    # a NULL monomial list with a positive count
+    s, keep = jet._spec_struct(sp)
+    s.mono[0] = ctypes.cast(None, ctypes.POINTER(jet.JetMonomial))
+    st, msg = _noalloc_status(s, 2, [2, 20, 1], needed)
+    assert st == 1 and "monomial list" in msg
+    # a needed multi-index in a coordinate beyond d_in
+    s, keep = jet._spec_struct(sp)
+    st, msg = _noalloc_status(s, 2, [2, 20, 1], needed + [(0, 0, 1)])
+    assert st == 1 and "coordinate >= d_in" in msg
+    # a residual factor differentiating a coordinate beyond d_in
+    bad = specs.Spec("bad", 2, 1, [[(1.0, [(0, (0, 0, 1))])]])
+    s, keep = jet._spec_struct(bad)
+    st, msg = _noalloc_status(s, 2, [2, 20, 1], needed)
+    assert st == 1 and "coordinate >= d_in" in msg

@@ -45,48 +45,86 @@ def test_tc_batch_matches_solo_and_oracle():
 
 @pytest.mark.parametrize("prec", ["bf16", "fp32"])
 def test_batch_train_step_graph_replay_equals_eager(prec):
+    """A captured batched train step with the Adam step counter in device
+    memory: three replays of one graph equal three eager steps 1, 2, 3
+    (bitwise), and the counter reads 3 afterwards."""
     from paper_2606_29702_gb300 import jet
     insts, plans, ps, xs = _ensemble(2, 2, (500, 3000), 21, prec)
     b = jet.Batch(plans)
-    p_e = [p.clone() for p in ps]
-    m_e = [torch.zeros_like(p) for p in ps]
-    v_e = [torch.zeros_like(p) for p in ps]
-    p_g = [p.clone() for p in ps]
-    m_g = [torch.zeros_like(p) for p in ps]
-    v_g = [torch.zeros_like(p) for p in ps]
-    loss_e = torch.empty(len(plans), dtype=torch.float64, device="cuda")
-    loss_g = torch.empty(len(plans), dtype=torch.float64, device="cuda")
     lr = float(np.float32(1e-3))
-    # eager: three steps
+
+    def state():
+        return [p.clone() for p in ps], [torch.zeros_like(p) for p in ps], [torch.zeros_like(p) for p in ps]
+
+    p_e, m_e, v_e = state()
+    loss_e = torch.empty(len(plans), dtype=torch.float64, device="cuda")
     for step in (1, 2, 3):
         b.train_step(p_e, m_e, v_e, step, lr, xs, loss=loss_e)
-    # graph: warm up once eagerly on a side stream, capture step 2, replay twice
-    b.train_step(p_g, m_g, v_g, 1, lr, xs, loss=loss_g)
+    # the device counter, eagerly: same steps, same bits
+    p_d, m_d, v_d = state()
+    ctr_d = torch.zeros(1, dtype=torch.int64, device="cuda")
+    loss_d = torch.empty_like(loss_e)
+    for _ in range(3):
+        b.train_step_dev(p_d, m_d, v_d, ctr_d, lr, xs, loss=loss_d)
+    # captured once (a warm-up call on a scratch copy first), replayed three times
+    p_g, m_g, v_g = state()
+    ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
+    loss_g = torch.empty_like(loss_e)
+    p_w, m_w, v_w = state()
+    b.train_step_dev(p_w, m_w, v_w, torch.zeros(1, dtype=torch.int64, device="cuda"), lr, xs)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
         with torch.cuda.graph(g, stream=s):
-            b.train_step(p_g, m_g, v_g, 2, lr, xs, loss=loss_g)
+            b.train_step_dev(p_g, m_g, v_g, ctr, lr, xs, loss=loss_g, stream=s)
     torch.cuda.synchronize()
-    g.replay()  # step 2 (capture does not execute)
+    assert int(ctr.item()) == 0  # capture does not execute
+    for _ in range(3):
+        g.replay()
     torch.cuda.synchronize()
-    step2 = [p.clone() for p in p_g]
-    g.replay()  # replays the same step index: Adam bias correction of step 2 again
-    torch.cuda.synchronize()
-    # reference for "step 2 applied twice" from the eager state after step 2
-    p_r = [p.clone() for p in ps]
-    m_r = [torch.zeros_like(p) for p in ps]
-    v_r = [torch.zeros_like(p) for p in ps]
-    loss_r = torch.empty_like(loss_e)
-    for step in (1, 2, 2):
-        b.train_step(p_r, m_r, v_r, step, lr, xs, loss=loss_r)
-    torch.cuda.synchronize()
+    assert int(ctr.item()) == 3 and int(ctr_d.item()) == 3
     for i in range(len(plans)):
-        assert torch.equal(p_g[i], p_r[i])
-        assert not torch.equal(step2[i], p_g[i])
-    assert torch.equal(loss_g, loss_r)
+        assert torch.equal(p_d[i], p_e[i]) and torch.equal(m_d[i], m_e[i]) and torch.equal(v_d[i], v_e[i])
+        assert torch.equal(p_g[i], p_e[i]) and torch.equal(m_g[i], m_e[i]) and torch.equal(v_g[i], v_e[i])
+    assert torch.equal(loss_g, loss_e) and torch.equal(loss_d, loss_e)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32", "fp64"])
+def test_plan_train_step_graph_replay_equals_eager(prec):
+    """jet_train_step_dev on one plan: three replays of a captured step equal
+    jet_train_step with steps 1, 2, 3 (bitwise)."""
+    import math
+    from paper_2606_29702_gb300 import jet, specs
+    widths = [2, 64, 64, 64, 1]
+    plan = jet.Plan(specs.burgers(0.01 / math.pi), widths, prec)
+    dt = plan.dtype
+    layers = wl.xavier_layers(widths, 5, bias_std=0.1)
+    x = torch.tensor(wl.points([(-1, 1), (0, 1)], 1500, 6), dtype=dt, device="cuda")
+    p0 = torch.tensor(wl.pack(layers), dtype=dt, device="cuda")
+    lr = float(np.float32(1e-3))
+    p_e, m_e, v_e = p0.clone(), torch.zeros_like(p0), torch.zeros_like(p0)
+    for step in (1, 2, 3):
+        loss_e = plan.train_step(p_e, m_e, v_e, step, lr, x)
+    p_w, m_w, v_w = p0.clone(), torch.zeros_like(p0), torch.zeros_like(p0)
+    plan.train_step_dev(p_w, m_w, v_w, torch.zeros(1, dtype=torch.int64, device="cuda"), lr, x)
+    torch.cuda.synchronize()
+    p_g, m_g, v_g = p0.clone(), torch.zeros_like(p0), torch.zeros_like(p0)
+    ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
+    loss_g = torch.empty((), dtype=torch.float64, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.train_step_dev(p_g, m_g, v_g, ctr, lr, x, loss=loss_g, stream=s)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    assert int(ctr.item()) == 3
+    assert torch.equal(p_g, p_e) and torch.equal(m_g, m_e) and torch.equal(v_g, v_e)
+    assert torch.equal(loss_g, loss_e)
 
 
 def test_full_ensemble_one_launch():

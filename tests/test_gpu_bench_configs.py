@@ -1,0 +1,214 @@
+"""Parity at the benchmarked configurations, through the same C ABI calls.
+
+Each case is a workload exactly as the benchmark runs it -- full depth and
+width, the benchmark's parameter seed (Xavier-normal, zero biases) and the
+benchmark's launch configuration (precision form, weight-gradient schedule,
+batching) -- evaluated on a seeded random subsample of S of the benchmark's
+own collocation points, so that the FP64 oracle (nested hyper-dual jets and a
+reverse tape) gives the exact residual and the exact gradient of the loss over
+the same S points.  Compared: the residual and the packed gradient by relative
+L2, the gradient by its largest elementwise error relative to its largest
+entry, the gradient cosine and the loss (the consistency columns of Table 1),
+and every output-jet channel separately.
+
+Each bound is stated per (workload, form, schedule) and sits at about twice
+the error measured on a GB300: a property of the operand precision (BF16
+rounding of the jet operands compounded over the layers and amplified with
+derivative order; FP32 rounding of the SIMT form), not of the method.
+"""
+import numpy as np
+import pytest
+
+from _common import cosine, oracle_family, oracle_source, rel_l2
+from paper_2606_29702_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+STORE_BUDGET = 4 << 30
+
+# (workload, form, schedule) -> (residual rel-L2, gradient rel-L2, gradient max-error / max |g|)
+BOUNDS = {
+    ("ks_2x64x5", "fp32", "tile"): (1e-5, 1e-5, 1e-5),
+    ("ks_2x64x5", "bf16", "tile"): (6e-2, 6e-2, 6e-2),
+    ("ks_2x64x5", "bf16x3", "tile"): (6e-2, 6e-2, 6e-2),
+    ("ns_psi_3x128x6", "fp32", "tile"): (1e-5, 1e-5, 1e-5),
+    ("ns_psi_3x128x6", "bf16", "tile"): (6e-2, 6e-2, 6e-2),
+    ("ns_psi_3x128x6", "bf16x3", "tile"): (6e-2, 6e-2, 6e-2),
+    ("helmholtz_3x256x8", "fp32", "tile"): (1e-5, 1e-5, 1e-5),
+    ("helmholtz_3x256x8", "bf16", "tile"): (6e-2, 6e-2, 6e-2),
+    ("helmholtz_3x256x8", "bf16", "store"): (6e-2, 6e-2, 6e-2),
+}
+# per output-jet channel, relative L2 over the sample: (workload, form) -> bound
+CHANNEL_BOUNDS = {
+    ("ks_2x64x5", "fp32"): 1e-5,
+    ("ks_2x64x5", "bf16"): 1e-1,
+    ("ns_psi_3x128x6", "fp32"): 1e-5,
+    ("ns_psi_3x128x6", "bf16"): 1e-1,
+    ("ns_psi_3x128x6", "bf16x3"): 1e-1,
+    ("helmholtz_3x256x8", "fp32"): 1e-5,
+    ("helmholtz_3x256x8", "bf16"): 1e-1,
+}
+# ensemble members (batched launch, S points each): form -> (gradient rel-L2, loss rel)
+ENSEMBLE_BOUNDS = {"bf16": (6e-2, 6e-2), "fp32": (1e-5, 1e-5)}
+S_POINTS = {"ks_2x64x5": 1024, "ns_psi_3x128x6": 512, "helmholtz_3x256x8": 512}
+
+
+def _sample(name, S):
+    """The benchmark's points, parameters and source, restricted to S of its points."""
+    spec = dict(wl.WORKLOADS[name])
+    X_full = wl.points(spec["domain"], spec["N"], spec["seed_pts"])
+    idx = np.sort(np.random.default_rng(17).choice(spec["N"], S, replace=False))
+    X = X_full[idx]
+    layers = wl.xavier_layers(spec["widths"], spec["seed_par"])
+    return spec, X, layers, oracle_source(spec["family"], spec["coefs"], X)
+
+
+def _plan(spec, form, schedule, sp=None, needed=None):
+    from paper_2606_29702_gb300 import jet, specs
+    sp = sp or specs.by_name(spec["family"], **spec["coefs"])
+    kw = dict(store=True, mem_budget=STORE_BUDGET) if schedule == "store" else {}
+    return jet.Plan(sp, spec["widths"], form, needed=needed, **kw)
+
+
+@pytest.mark.parametrize("name,form,schedule", sorted(BOUNDS), ids=["-".join(k) for k in sorted(BOUNDS)])
+def test_bench_config_matches_oracle(name, form, schedule):
+    import oracle
+    S = S_POINTS[name]
+    spec, X, layers, src = _sample(name, S)
+    L, r_ref, g_ref = oracle.loss_and_grad(oracle_family(spec["family"], spec["coefs"]), layers, X, source=src)
+    g_ref = wl.pack(g_ref)
+    plan = _plan(spec, form, schedule)
+    dt = plan.dtype
+    p = torch.tensor(wl.pack(layers), dtype=dt, device="cuda")
+    x = torch.tensor(X, dtype=dt, device="cuda")
+    s = None if src is None else torch.tensor(src, dtype=dt, device="cuda")
+    g, loss, r = plan.backward(p, x, s, want_r=True)
+    torch.cuda.synchronize()
+    r = r.cpu().double().numpy()
+    g = g.cpu().double().numpy()
+    er = rel_l2(r, r_ref)
+    eg = rel_l2(g, g_ref)
+    em = float(np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref)))
+    cs = cosine(g, g_ref)
+    el = abs(float(loss) - L) / abs(L)
+    info = plan.info()
+    print("BENCHCFG %s %s %s: residual %.3e gradient %.3e grad-max %.3e cosine %.10f loss %.3e (P=%d, %s)"
+          % (name, form, schedule, er, eg, em, cs, el, info["tile_points"], info["class_name"]))
+    tr, tg, tm = BOUNDS[(name, form, schedule)]
+    assert er <= tr and eg <= tg and em <= tm
+    assert el <= 2 * tr
+    assert cs >= 1.0 - tg ** 2
+
+
+def _channel_groups(sp):
+    """Single-channel 'residuals' of the output jet, four per plan: (output, alpha)."""
+    chans = sp.closure()
+    items = [(0, al) for al in chans]
+    for o in range(1, sp.n_out):
+        # further outputs: the channels their residual terms read
+        used = sorted({al for comp in sp.components for _, facs in comp for oo, al in facs if oo == o})
+        items += [(o, al) for al in used]
+    return chans, [items[i:i + 4] for i in range(0, len(items), 4)]
+
+
+@pytest.mark.parametrize("name,form", sorted(CHANNEL_BOUNDS), ids=["-".join(k) for k in sorted(CHANNEL_BOUNDS)])
+def test_bench_config_per_channel(name, form):
+    import oracle
+    from paper_2606_29702_gb300 import specs
+    S = min(S_POINTS[name], 512)
+    spec, X, layers, _ = _sample(name, S)
+    sp = specs.by_name(spec["family"], **spec["coefs"])
+    chans, groups = _channel_groups(sp)
+    ref = oracle.network_jets(layers, X, chans)
+    x = None
+    worst = 0.0
+    rows = []
+    for grp in groups:
+        gs = specs.Spec("chan", sp.d_in, sp.n_out, [[(1.0, [(o, al)])] for o, al in grp])
+        plan = _plan(spec, form, "tile", sp=gs, needed=chans)
+        if x is None:
+            dt = plan.dtype
+            p = torch.tensor(wl.pack(layers), dtype=dt, device="cuda")
+            x = torch.tensor(X, dtype=dt, device="cuda")
+        r, _ = plan.forward(p, x)
+        torch.cuda.synchronize()
+        r = r.cpu().double().numpy()
+        for j, (o, al) in enumerate(grp):
+            e = rel_l2(r[:, j], ref[al][:, o])
+            rows.append("u%d_%s %.2e" % (o, "".join(map(str, al)), e))
+            worst = max(worst, e)
+    print("CHANNELS %s %s: %s" % (name, form, ", ".join(rows)))
+    assert worst <= CHANNEL_BOUNDS[(name, form)]
+
+
+@pytest.mark.parametrize("form", sorted(ENSEMBLE_BOUNDS))
+def test_ensemble_members_match_oracle(form):
+    """The 64-instance ensemble in one batched launch, every member on the
+    first 128 of its points, each member's gradient and loss against the
+    oracle."""
+    import oracle
+    from oracle import residuals as R
+    from paper_2606_29702_gb300 import jet, specs
+    S = 128
+    insts = wl.ensemble()
+    plans, ps, xs = [], [], []
+    for ins in insts:
+        plans.append(jet.Plan(specs.by_name(ins["family"], **ins["coefs"]), ins["widths"], form))
+        ps.append(torch.tensor(wl.pack(ins["layers"]), dtype=torch.float32, device="cuda"))
+        xs.append(torch.tensor(ins["X"][:S], dtype=torch.float32, device="cuda"))
+    grads, losses = jet.Batch(plans).backward(ps, xs)
+    torch.cuda.synchronize()
+    eg_max = el_max = 0.0
+    for i, ins in enumerate(insts):
+        L, _, g_ref = oracle.loss_and_grad(R.by_name(ins["family"], **ins["coefs"]), ins["layers"], ins["X"][:S])
+        eg_max = max(eg_max, rel_l2(grads[i].cpu().numpy(), wl.pack(g_ref)))
+        el_max = max(el_max, abs(float(losses[i]) - L) / abs(L))
+    print("ENSEMBLE %s: worst member gradient %.3e loss %.3e" % (form, eg_max, el_max))
+    tg, tl = ENSEMBLE_BOUNDS[form]
+    assert eg_max <= tg and el_max <= tl
+
+
+# Adam trajectories of the Helmholtz network (small-N proxy of the 1000-step
+# run): form -> bound on |L_gpu(k) - L_oracle(k)| / L_oracle(k) over the steps
+TRAJ_STEPS = 20
+TRAJ_BOUNDS = {("bf16", "store"): 6e-2, ("bf16", "tile"): 6e-2, ("fp32", "tile"): 1e-4}
+
+
+@pytest.mark.parametrize("form,schedule", sorted(TRAJ_BOUNDS), ids=["-".join(k) for k in sorted(TRAJ_BOUNDS)])
+def test_helmholtz_adam_trajectory_matches_oracle(form, schedule):
+    """The first steps of the Helmholtz 3->256x8->1 training run (Adam, lr 1e-3,
+    the benchmark's initialisation) on 256 of its points: the loss before every
+    step against an FP64 oracle trajectory (oracle gradient + oracle Adam)."""
+    import oracle
+    name = "helmholtz_3x256x8"
+    spec, X, layers, src = _sample(name, 256)
+    fam = oracle_family(spec["family"], spec["coefs"])
+    lr = float(np.float32(1e-3))  # the ABI passes lr as a C float
+    theta = wl.pack(layers)
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    L_ref = []
+    for k in range(1, TRAJ_STEPS + 1):
+        L, _, g = oracle.loss_and_grad(fam, wl.unpack(theta, spec["widths"]), X, source=src)
+        L_ref.append(L)
+        theta, m, v = oracle.adam_step(theta, m, v, wl.pack(g), k, lr=lr)
+    plan = _plan(spec, form, schedule)
+    dt = plan.dtype
+    p = torch.tensor(wl.pack(layers), dtype=dt, device="cuda")
+    mg = torch.zeros_like(p)
+    vg = torch.zeros_like(p)
+    x = torch.tensor(X, dtype=dt, device="cuda")
+    s = None if src is None else torch.tensor(src, dtype=dt, device="cuda")
+    ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
+    hist = torch.empty(TRAJ_STEPS, dtype=torch.float64, device="cuda")
+    for k in range(TRAJ_STEPS):
+        plan.train_step_dev(p, mg, vg, ctr, lr, x, s, loss=hist[k])
+    torch.cuda.synchronize()
+    assert int(ctr.item()) == TRAJ_STEPS
+    h = hist.cpu().numpy()
+    errs = np.abs(h - np.array(L_ref)) / np.array(L_ref)
+    print("TRAJ %s %s: loss %.6e -> %.6e (oracle %.6e -> %.6e), worst step error %.3e, per step %s"
+          % (form, schedule, h[0], h[-1], L_ref[0], L_ref[-1], errs.max(), " ".join("%.1e" % e for e in errs)))
+    assert L_ref[-1] < L_ref[0]  # the oracle run trains
+    assert errs.max() <= TRAJ_BOUNDS[(form, schedule)]
