@@ -37,6 +37,13 @@
  *   * Errors: every call returns a jet_status and never aborts; a thread-
  *     local message is available from jet_last_error().  Shape and spec
  *     errors are caught by jet_plan_create.
+ *   * CUDA graphs: the compute calls of a plan or batch may be recorded by
+ *     stream capture once the same call has run outside capture (which sizes
+ *     any store and loads the kernels).  A call being captured allocates
+ *     nothing and reads nothing back to the host; a bounded device wait that
+ *     times out during a replay is reported by the next call made outside
+ *     capture.  jet_train_step_dev keeps the Adam step on the device, so
+ *     replays advance it.
  */
 #ifndef JET_H_
 #define JET_H_

@@ -25,6 +25,11 @@ Families and the passages they follow:
       r_v = v_t + u v_x + v v_y + p_y - nu (v_xx + v_yy)
   The continuity residual of Eq. 16 vanishes identically for u = psi_y,
   v = -psi_x and is not assembled.
+* Navier-Stokes in primitive variables, Eq. 16 as printed: inputs (x, y),
+  outputs (u, v, p), steady, Re = 100 in the lid-driven cavity of Sec. 3.1.1:
+      r_c = u_x + v_y
+      r_u = u u_x + v u_y + p_x - (u_xx + u_yy) / Re
+      r_v = u v_x + v v_y + p_y - (v_xx + v_yy) / Re
 * Generic: a list of components, each a sum of monomials coef * prod_j
   d^{alpha_j} u_{o_j}, minus an optional per-point source column.
 
@@ -121,6 +126,24 @@ def navier_stokes_psi(nu=0.01):
     return fam
 
 
+def navier_stokes_uvp(Re=100.0):
+    # inputs (x, y); outputs 0 = u, 1 = v, 2 = p
+    O, DX, DY, DXX, DYY = (0, 0), (1, 0), (0, 1), (2, 0), (0, 2)
+    need = [O, DX, DY, DXX, DYY]
+
+    def fn(U, X, source):
+        u, v = U[(0, O)], U[(1, O)]
+        u_x, u_y, v_x, v_y = U[(0, DX)], U[(0, DY)], U[(1, DX)], U[(1, DY)]
+        p_x, p_y = U[(2, DX)], U[(2, DY)]
+        lap_u = U[(0, DXX)] + U[(0, DYY)]
+        lap_v = U[(1, DXX)] + U[(1, DYY)]
+        r_c = u_x + v_y
+        r_u = u * u_x + v * u_y + p_x - lap_u * (1.0 / Re)
+        r_v = u * v_x + v * v_y + p_y - lap_v * (1.0 / Re)
+        return [r_c, r_u, r_v]
+    return Family("ns_uvp", 2, 3, need, fn)
+
+
 def monomial_family(d_in, n_out, components, has_source=False):
     """Generic residual: components[c] = list of (coef, [(o, alpha), ...]).
 
@@ -152,5 +175,6 @@ def by_name(name, **kw):
         "allen_cahn": allen_cahn,
         "helmholtz": helmholtz,
         "ns_psi": navier_stokes_psi,
+        "ns_uvp": navier_stokes_uvp,
     }
     return table[name](**kw)

@@ -16,12 +16,23 @@ code, specialised at compile time, for
 
 phi = tanh, with p[k] = phi^(k)(z_0) supplied by ``tanh_derivs``.
 
+The compiled classes are the generic full-order sets d1o4, d2o2 and d3o2, the
+exact closure of every residual family in the package's ``specs.py`` (read at
+build time, so a family added there gets its own class on the next build), and
+the sets named in the environment variable JET_EXTRA_CLASSES
+('d:alpha,alpha,...;...', e.g. '2:00,10,01,11').  A plan carries the smallest
+compiled class that contains its closure.
+
 Run: python gen_closures.py <out.h>   (the build does this).
 """
 
+import importlib.util
 import itertools
+import os
 import sys
 from collections import OrderedDict
+
+HERE = os.path.dirname(os.path.abspath(__file__))
 
 # name -> (d, list of multi-indices); channel 0 is the value, channels are
 # sorted by total order so the highest-order channels form the last block.
@@ -41,14 +52,65 @@ def _sort(chans):
     return sorted(set(tuple(c) for c in chans), key=lambda a: (sum(a), tuple(-x for x in a)))
 
 
-CLASSES["d1o4"] = (1, _sort([(k,) for k in range(5)]))
-CLASSES["xt_burgers"] = (2, _sort([(0, 0), (1, 0), (0, 1), (2, 0)]))
-CLASSES["xt_ks"] = (2, _sort([(0, 0), (1, 0), (0, 1), (2, 0), (3, 0), (4, 0)]))
+def _load_specs():
+    """The package's residual-family table (specs.py), loaded by path: it is
+    plain Python with no dependencies."""
+    sp = importlib.util.spec_from_file_location("jet_specs_table", os.path.join(HERE, os.pardir, "specs.py"))
+    mod = importlib.util.module_from_spec(sp)
+    sp.loader.exec_module(mod)
+    return mod
+
+
+def _add(name, d, chans):
+    """Register a channel set unless an identical one is already compiled."""
+    chans = _sort(chans)
+    for d2, c2 in CLASSES.values():
+        if d2 == d and c2 == chans:
+            return
+    CLASSES[name] = (d, chans)
+
+
+def _parse_extra(text):
+    """JET_EXTRA_CLASSES: 'd:alpha,alpha,...;d:...' with alpha as digits, e.g.
+    '2:00,10,01,11' adds the set {(0,0), (1,0), (0,1), (1,1)} (closed downward
+    here)."""
+    out = []
+    for item in filter(None, (t.strip() for t in text.split(";"))):
+        d, rest = item.split(":")
+        d = int(d)
+        chans = [tuple(int(ch) for ch in a.strip()) for a in rest.split(",") if a.strip()]
+        if any(len(a) != d for a in chans):
+            raise ValueError("JET_EXTRA_CLASSES: multi-index of the wrong length in %r" % item)
+        out.append((d, _downward(chans, d)))
+    return out
+
+
+def _downward(chans, d):
+    out, stack = set(), [tuple(a) for a in chans] + [tuple([0] * d)]
+    while stack:
+        a = stack.pop()
+        if a in out:
+            continue
+        out.add(a)
+        for i, k in enumerate(a):
+            if k:
+                stack.append(a[:i] + (k - 1,) + a[i + 1:])
+    return sorted(out)
+
+
+# Generic full-order sets (any residual up to that order in 1, 2 or 3
+# coordinates), then the exact closure of every residual family of specs.py
+# (Sec. 2.2: each residual carries exactly the channels it needs), then any
+# sets named by the build environment.
+CLASSES["d1o4"] = (1, _sort(_full(1, 4)))
 CLASSES["d2o2"] = (2, _sort(_full(2, 2)))
-CLASSES["xyz_lap"] = (3, _sort([(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2)]))
 CLASSES["d3o2"] = (3, _sort(_full(3, 2)))
-CLASSES["xyt_ns3"] = (3, _sort([(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (1, 1, 0), (0, 2, 0),
-                                (1, 0, 1), (0, 1, 1), (3, 0, 0), (2, 1, 0), (1, 2, 0), (0, 3, 0)]))
+_SPECS = _load_specs()
+for _fam, _coefs in _SPECS.FAMILY_DEFAULTS.items():
+    _s = _SPECS.by_name(_fam, **_coefs)
+    _add(_fam, _s.d_in, _s.closure())
+for _i, (_d, _chans) in enumerate(_parse_extra(os.environ.get("JET_EXTRA_CLASSES", ""))):
+    _add("extra%d" % _i, _d, _chans)
 
 
 def set_partitions(items):

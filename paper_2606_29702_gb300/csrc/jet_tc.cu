@@ -618,8 +618,17 @@ size_t tc_workspace_bytes(const TcPlan* t) { return t ? t->ws_bytes : 0; }
 
 namespace {
 
-jet_status check_err(TcPlan* t) {
-  // device-side wait time-outs of an earlier call surface here
+bool is_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// Device-side wait time-outs of an earlier call surface here.  While the
+// stream is being captured into a CUDA graph the event query (and the
+// read-back in run) would invalidate the capture: a time-out inside a replayed
+// graph surfaces at the next call made outside capture.
+jet_status check_err(TcPlan* t, cudaStream_t s) {
+  if (is_capturing(s)) return JET_OK;
   if (cudaEventQuery(t->err_ev) == cudaSuccess && *t->h_err != 0) {
     char buf[128];
     snprintf(buf, sizeof(buf), "a bounded device wait timed out in an earlier call (code %d)", *t->h_err);
@@ -709,8 +718,8 @@ jet_status store_too_small(const TcPlan* t, long long N) {
   return tfail(JET_ERR_OOM, msg);
 }
 
-void ensure_store(TcPlan* t, long long N) {
-  if (!t->wstore_budget || !t->wg_out || N < 1) return;
+void ensure_store(TcPlan* t, long long N, cudaStream_t s) {
+  if (!t->wstore_budget || !t->wg_out || N < 1 || is_capturing(s)) return;
   const long long tiles = (N + t->P - 1) / t->P;
   if (tiles <= t->wstore_tiles) return;
   const size_t need = (size_t)tiles * (size_t)t->wstore_tile_stride;
@@ -817,6 +826,7 @@ jet_status run(jet_plan_s* p, TcPlan* t, int mode, const TcInst& I, cudaStream_t
   }
   jet::plan_prof_end(p, s);
   if (e != cudaSuccess) return tcuda(e, "tc kernel launch");
+  if (is_capturing(s)) return JET_OK;
   e = cudaMemcpyAsync(t->h_err, t->err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaEventRecord(t->err_ev, s);
   return e == cudaSuccess ? JET_OK : tcuda(e, "tc error read-back");
@@ -826,7 +836,7 @@ jet_status run(jet_plan_s* p, TcPlan* t, int mode, const TcInst& I, cudaStream_t
 
 jet_status tc_forward(jet_plan_s* p, TcPlan* t, const void* params, const void* X, long long N, const void* source,
                       void* r_out, double* loss_out, cudaStream_t s) {
-  jet_status st = check_err(t);
+  jet_status st = check_err(t, s);
   if (st != JET_OK) return st;
   if (N == 0) {
     if (loss_out && cudaMemsetAsync(loss_out, 0, sizeof(double), s) != cudaSuccess) return tcuda(cudaGetLastError(), "memset");
@@ -853,14 +863,14 @@ jet_status tc_forward(jet_plan_s* p, TcPlan* t, const void* params, const void* 
 
 jet_status tc_backward(jet_plan_s* p, TcPlan* t, const void* params, const void* X, long long N, const void* source,
                        void* grad_out, void* r_out, double* loss_out, cudaStream_t s) {
-  jet_status st = check_err(t);
+  jet_status st = check_err(t, s);
   if (st != JET_OK) return st;
   if (N == 0) {
     cudaMemsetAsync(grad_out, 0, p->n_params * 4, s);
     if (loss_out) cudaMemsetAsync(loss_out, 0, sizeof(double), s);
     return JET_OK;
   }
-  ensure_store(t, N);
+  ensure_store(t, N, s);
   st = prep(p, t, params, s);
   if (st != JET_OK) return st;
   TcInst I;
@@ -885,9 +895,9 @@ jet_status tc_backward(jet_plan_s* p, TcPlan* t, const void* params, const void*
 jet_status tc_train_step(jet_plan_s* p, TcPlan* t, void* params, void* m, void* v, long long step,
                          long long* step_ctr, float lr, const void* X, long long N, const void* source,
                          double* loss_out, cudaStream_t s) {
-  jet_status st = check_err(t);
+  jet_status st = check_err(t, s);
   if (st != JET_OK) return st;
-  ensure_store(t, N);
+  ensure_store(t, N, s);
   st = prep(p, t, params, s);
   if (st != JET_OK) return st;
   TcInst I;

@@ -15,6 +15,12 @@ Families (coordinates in input order):
   the momentum residuals of Eq. 16 with the time derivative,
   r_u = psi_yt + psi_y psi_xy - psi_x psi_yy + p_x - nu (psi_xxy + psi_yyy),
   r_v = -psi_xt - psi_y psi_xx + psi_x psi_xy + p_y + nu (psi_xxx + psi_xyy).
+* ns_uvp(Re), inputs (x, y), outputs (u, v, p): the steady incompressible
+  Navier-Stokes residuals of Eq. 16 in primitive variables,
+  r_c = u_x + v_y,
+  r_u = u u_x + v u_y + p_x - (u_xx + u_yy) / Re,
+  r_v = u v_x + v v_y + p_y - (v_xx + v_yy) / Re
+  (closure {0, x, y, xx, yy}: no mixed channel).
 """
 
 import math
@@ -91,9 +97,27 @@ def ns_psi(nu=0.01):
     return Spec("ns_psi", 3, 2, [ru, rv])
 
 
+def ns_uvp(Re=100.0):
+    U, X, Y, XX, YY = (0, 0), (1, 0), (0, 1), (2, 0), (0, 2)
+    u, v, p = 0, 1, 2
+    rc = [(1.0, [(u, X)]), (1.0, [(v, Y)])]
+    ru = [(1.0, [(u, U), (u, X)]), (1.0, [(v, U), (u, Y)]), (1.0, [(p, X)]),
+          (-1.0 / Re, [(u, XX)]), (-1.0 / Re, [(u, YY)])]
+    rv = [(1.0, [(u, U), (v, X)]), (1.0, [(v, U), (v, Y)]), (1.0, [(p, Y)]),
+          (-1.0 / Re, [(v, XX)]), (-1.0 / Re, [(v, YY)])]
+    return Spec("ns_uvp", 2, 3, [rc, ru, rv])
+
+
+FAMILIES = {"burgers": burgers, "ks": ks, "allen_cahn": allen_cahn, "helmholtz": helmholtz, "ns_psi": ns_psi,
+            "ns_uvp": ns_uvp}
+# representative coefficients of every family (the build derives each
+# family's compiled channel set from its closure, which they do not change)
+FAMILY_DEFAULTS = {"burgers": dict(nu=0.01), "ks": dict(), "allen_cahn": dict(), "helmholtz": dict(),
+                   "ns_psi": dict(nu=0.01), "ns_uvp": dict(Re=100.0)}
+
+
 def by_name(name, **coefs):
-    return {"burgers": burgers, "ks": ks, "allen_cahn": allen_cahn, "helmholtz": helmholtz,
-            "ns_psi": ns_psi}[name](**coefs)
+    return FAMILIES[name](**coefs)
 
 
 def helmholtz_source(X, k=4.0 * math.pi):

@@ -20,6 +20,9 @@ involved in the residual loss):
   N_i uniform in [2048, 65536], bf16 operands.
 * ``helmholtz_3x256x8``: 3-D Helmholtz, k = 4 pi, 3->256x8->1, N = 1048576
   uniform on [-1,1]^3, bf16 operands, Adam lr 1e-3.
+* ``ns_uvp_2x64x6``: steady Navier-Stokes in primitive variables (u, v, p),
+  Re = 100 (Eq. 16), 2->64x6->3 as in Sec. 3.1.1, N = 10000 PDE points
+  uniform on the unit square, float32.
 """
 
 import math
@@ -35,6 +38,8 @@ WORKLOADS = {
                            N=262144, domain=[(0.0, 1.0)] * 3, precision="bf16", seed_pts=0, seed_par=1),
     "helmholtz_3x256x8": dict(family="helmholtz", coefs=dict(k=4.0 * math.pi), widths=[3] + [256] * 8 + [1],
                               N=1048576, domain=[(-1.0, 1.0)] * 3, precision="bf16", seed_pts=0, seed_par=1),
+    "ns_uvp_2x64x6": dict(family="ns_uvp", coefs=dict(Re=100.0), widths=[2] + [64] * 6 + [3],
+                          N=10000, domain=[(0.0, 1.0)] * 2, precision="fp32", seed_pts=0, seed_par=1),
 }
 
 

@@ -27,31 +27,40 @@ pytestmark = pytest.mark.gpu
 
 STORE_BUDGET = 4 << 30
 
-# (workload, form, schedule) -> (residual rel-L2, gradient rel-L2, gradient max-error / max |g|)
+# (workload, form, schedule) -> (residual rel-L2, gradient rel-L2, gradient max-error / max |g|).
+# FP32 keeps the stated FP32 bound (1e-5); the measured FP32 errors are 1e-7 .. 1e-6.
 BOUNDS = {
     ("ks_2x64x5", "fp32", "tile"): (1e-5, 1e-5, 1e-5),
-    ("ks_2x64x5", "bf16", "tile"): (6e-2, 6e-2, 6e-2),
-    ("ks_2x64x5", "bf16x3", "tile"): (6e-2, 6e-2, 6e-2),
+    ("ks_2x64x5", "bf16", "tile"): (1.8e-2, 8e-3, 9e-3),
+    ("ks_2x64x5", "bf16x3", "tile"): (1.6e-2, 7.5e-3, 8.5e-3),
     ("ns_psi_3x128x6", "fp32", "tile"): (1e-5, 1e-5, 1e-5),
-    ("ns_psi_3x128x6", "bf16", "tile"): (6e-2, 6e-2, 6e-2),
-    ("ns_psi_3x128x6", "bf16x3", "tile"): (6e-2, 6e-2, 6e-2),
+    ("ns_psi_3x128x6", "bf16", "tile"): (3e-2, 2.4e-2, 2e-2),
+    ("ns_psi_3x128x6", "bf16x3", "tile"): (3e-2, 2.4e-2, 2e-2),
     ("helmholtz_3x256x8", "fp32", "tile"): (1e-5, 1e-5, 1e-5),
-    ("helmholtz_3x256x8", "bf16", "tile"): (6e-2, 6e-2, 6e-2),
-    ("helmholtz_3x256x8", "bf16", "store"): (6e-2, 6e-2, 6e-2),
+    ("helmholtz_3x256x8", "bf16", "tile"): (8e-3, 3.5e-2, 1e-2),
+    ("helmholtz_3x256x8", "bf16", "store"): (8e-3, 3.5e-2, 1e-2),
+    ("ns_uvp_2x64x6", "fp32", "tile"): (1e-5, 1e-5, 1e-5),
+    ("ns_uvp_2x64x6", "bf16", "tile"): (6e-2, 6e-2, 6e-2),
 }
-# per output-jet channel, relative L2 over the sample: (workload, form) -> bound
+# per output-jet channel, relative L2 over the sample:
+# (workload, form) -> {(output, derivative order): bound}
 CHANNEL_BOUNDS = {
-    ("ks_2x64x5", "fp32"): 1e-5,
-    ("ks_2x64x5", "bf16"): 1e-1,
-    ("ns_psi_3x128x6", "fp32"): 1e-5,
-    ("ns_psi_3x128x6", "bf16"): 1e-1,
-    ("ns_psi_3x128x6", "bf16x3"): 1e-1,
-    ("helmholtz_3x256x8", "fp32"): 1e-5,
-    ("helmholtz_3x256x8", "bf16"): 1e-1,
+    ("ks_2x64x5", "fp32"): {(0, k): 1e-5 for k in range(5)},
+    ("ks_2x64x5", "bf16"): {(0, 0): 2e-2, (0, 1): 2.5e-2, (0, 2): 2.6e-2, (0, 3): 2.4e-2, (0, 4): 2.5e-2},
+    ("ns_psi_3x128x6", "fp32"): {(0, 0): 1e-5, (0, 1): 1e-5, (0, 2): 1e-5, (0, 3): 1e-5, (1, 1): 1e-5},
+    ("ns_psi_3x128x6", "bf16"): {(0, 0): 1e-2, (0, 1): 1.3e-2, (0, 2): 1.7e-2, (0, 3): 1.6e-2, (1, 1): 9e-2},
+    # the split products on the third-order channels: their own, tighter bound
+    ("ns_psi_3x128x6", "bf16x3"): {(0, 0): 1e-2, (0, 1): 1.3e-2, (0, 2): 1.7e-2, (0, 3): 1.3e-2, (1, 1): 9e-2},
+    ("helmholtz_3x256x8", "fp32"): {(0, 0): 1e-5, (0, 1): 1e-5, (0, 2): 1e-5},
+    ("helmholtz_3x256x8", "bf16"): {(0, 0): 9e-2, (0, 1): 1.65e-1, (0, 2): 5.6e-2},
 }
-# ensemble members (batched launch, S points each): form -> (gradient rel-L2, loss rel)
-ENSEMBLE_BOUNDS = {"bf16": (6e-2, 6e-2), "fp32": (1e-5, 1e-5)}
-S_POINTS = {"ks_2x64x5": 1024, "ns_psi_3x128x6": 512, "helmholtz_3x256x8": 512}
+# ensemble members (batched launch, S points each): form -> (gradient, loss) bound.
+# BF16: relative to each member's own sensitivity s_i to BF16 rounding (the
+# oracle's gradient change when only the weights are rounded to BF16), bound
+# a * s_i + b; several deep members change their gradient by 10-27% under that
+# rounding alone.  FP32: the stated FP32 bound.
+ENSEMBLE_BOUNDS = {"bf16": ((2.0, 2e-2), (2.0, 2e-2)), "fp32": ((0.0, 1e-5), (0.0, 1e-5))}
+S_POINTS = {"ks_2x64x5": 1024, "ns_psi_3x128x6": 512, "helmholtz_3x256x8": 512, "ns_uvp_2x64x6": 1024}
 
 
 def _sample(name, S):
@@ -122,7 +131,8 @@ def test_bench_config_per_channel(name, form):
     chans, groups = _channel_groups(sp)
     ref = oracle.network_jets(layers, X, chans)
     x = None
-    worst = 0.0
+    bounds = CHANNEL_BOUNDS[(name, form)]
+    bad = []
     rows = []
     for grp in groups:
         gs = specs.Spec("chan", sp.d_in, sp.n_out, [[(1.0, [(o, al)])] for o, al in grp])
@@ -137,9 +147,15 @@ def test_bench_config_per_channel(name, form):
         for j, (o, al) in enumerate(grp):
             e = rel_l2(r[:, j], ref[al][:, o])
             rows.append("u%d_%s %.2e" % (o, "".join(map(str, al)), e))
-            worst = max(worst, e)
+            if e > bounds[(o, sum(al))]:
+                bad.append(rows[-1])
     print("CHANNELS %s %s: %s" % (name, form, ", ".join(rows)))
-    assert worst <= CHANNEL_BOUNDS[(name, form)]
+    assert not bad, bad
+
+
+def _bf16(a):
+    """Round to the nearest BF16 value (test-side helper, via torch on the CPU)."""
+    return torch.tensor(np.asarray(a), dtype=torch.float32).to(torch.bfloat16).double().numpy()
 
 
 @pytest.mark.parametrize("form", sorted(ENSEMBLE_BOUNDS))
@@ -159,20 +175,31 @@ def test_ensemble_members_match_oracle(form):
         xs.append(torch.tensor(ins["X"][:S], dtype=torch.float32, device="cuda"))
     grads, losses = jet.Batch(plans).backward(ps, xs)
     torch.cuda.synchronize()
-    eg_max = el_max = 0.0
+    (ag, bg), (al_, bl) = ENSEMBLE_BOUNDS[form]
+    rows, bad = [], []
     for i, ins in enumerate(insts):
-        L, _, g_ref = oracle.loss_and_grad(R.by_name(ins["family"], **ins["coefs"]), ins["layers"], ins["X"][:S])
-        eg_max = max(eg_max, rel_l2(grads[i].cpu().numpy(), wl.pack(g_ref)))
-        el_max = max(el_max, abs(float(losses[i]) - L) / abs(L))
-    print("ENSEMBLE %s: worst member gradient %.3e loss %.3e" % (form, eg_max, el_max))
-    tg, tl = ENSEMBLE_BOUNDS[form]
-    assert eg_max <= tg and el_max <= tl
+        fam = R.by_name(ins["family"], **ins["coefs"])
+        L, _, g_ref = oracle.loss_and_grad(fam, ins["layers"], ins["X"][:S])
+        g_ref = wl.pack(g_ref)
+        eg = rel_l2(grads[i].cpu().numpy(), g_ref)
+        el = abs(float(losses[i]) - L) / abs(L)
+        sg = sl = 0.0
+        if ag or al_:
+            Lb, _, gb = oracle.loss_and_grad(fam, [(_bf16(W), b) for W, b in ins["layers"]], ins["X"][:S])
+            sg, sl = rel_l2(wl.pack(gb), g_ref), abs(Lb - L) / abs(L)
+        rows.append((eg, el, sg, sl, i))
+        if eg > ag * sg + bg or el > al_ * sl + bl:
+            bad.append(rows[-1])
+    rows.sort(reverse=True)
+    print("ENSEMBLE %s: worst members (gradient err, loss err, BF16 sensitivity of gradient, of loss, member): %s"
+          % (form, "; ".join("%.2e %.2e %.2e %.2e #%d" % r for r in rows[:6])))
+    assert not bad, bad
 
 
 # Adam trajectories of the Helmholtz network (small-N proxy of the 1000-step
 # run): form -> bound on |L_gpu(k) - L_oracle(k)| / L_oracle(k) over the steps
 TRAJ_STEPS = 20
-TRAJ_BOUNDS = {("bf16", "store"): 6e-2, ("bf16", "tile"): 6e-2, ("fp32", "tile"): 1e-4}
+TRAJ_BOUNDS = {("bf16", "store"): 3.5e-2, ("bf16", "tile"): 3.5e-2, ("fp32", "tile"): 1.2e-4}
 
 
 @pytest.mark.parametrize("form,schedule", sorted(TRAJ_BOUNDS), ids=["-".join(k) for k in sorted(TRAJ_BOUNDS)])

@@ -49,6 +49,8 @@ CASES = [
     ("ns_psi_3x128x6", "fp64", 40, None),
     ("helmholtz_3x256x8", "fp32", 90, None),
     ("helmholtz_3x256x8", "fp64", 33, [3, 64, 64, 64, 1]),
+    ("ns_uvp_2x64x6", "fp32", 500, None),
+    ("ns_uvp_2x64x6", "fp64", 200, None),
 ]
 
 
@@ -276,3 +278,15 @@ def test_batch_matches_solo_runs():
         assert rel_l2(grads[i].cpu().numpy(), wl.pack(g_ref)) <= 1e-5
         assert rel_l2(grads[i].cpu().numpy(), solo[i][0].cpu().numpy()) <= 1e-6
         assert abs(float(losses[i]) - L) <= 1e-5 * abs(L)
+
+
+def test_ns_uvp_carries_exactly_its_closure():
+    """Eq. 16 needs {0, x, y, xx, yy} for (u, v) and {0, x, y} for p: the plan
+    carries the five-channel set built from the residual's spec, not a superset
+    with the mixed xy channel."""
+    jet, specs = _jet()
+    for prec in ("fp32", "bf16"):
+        plan = jet.Plan(specs.ns_uvp(100.0), [2, 64, 64, 3], prec)
+        info = plan.info()
+        assert info["class_name"] == "ns_uvp" and info["n_channels"] == 5
+        plan.close()

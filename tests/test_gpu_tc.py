@@ -2,11 +2,11 @@
 accumulation; BF16X3 adds split hi/lo products on the highest-order channels)
 against the FP64 oracle, through the C ABI.
 
-Stated bounds (relative L2 over points / over the packed gradient), set from
-measurement with headroom; they are properties of BF16 rounding of the jet
-operands compounded over layers and derivative order, not of the method:
-see TOL below.  Per-channel errors are measured by plans whose "residual" is a
-single output-jet channel.
+Stated bounds (relative L2 over points / over the packed gradient), one per
+(case, form), at about twice the error measured on a GB300; they are
+properties of BF16 rounding of the jet operands compounded over layers and
+derivative order, not of the method: see TOL below.  Per-channel errors are
+measured by plans whose "residual" is a single output-jet channel.
 """
 import math
 
@@ -28,9 +28,22 @@ CASES = [
     ("ks_w64", "ks", dict(c1=1.0, c2=1.0, c4=1.0), [2] + [64] * 5 + [1], [(0, 2 * math.pi), (0, 1)], 300),
     ("ns_psi_w128", "ns_psi", dict(nu=0.01), [3] + [128] * 4 + [2], [(0, 1)] * 3, 100),
     ("helmholtz_w256", "helmholtz", dict(k=4 * math.pi), [3] + [256] * 4 + [1], [(-1, 1)] * 3, 70),
+    ("ns_uvp_w64", "ns_uvp", dict(Re=100.0), [2] + [64] * 6 + [3], [(0, 1)] * 2, 300),
 ]
-# (residual rel-L2, gradient rel-L2) bounds per precision
-TOL = {"bf16": (6e-2, 6e-2), "bf16x3": (6e-2, 6e-2)}
+# (residual rel-L2, gradient rel-L2) bounds per (case, form)
+TOL = {
+    ("burgers_w32", "bf16"): (7e-3, 7e-3), ("burgers_w32", "bf16x3"): (7e-3, 7e-3),
+    ("burgers_L2", "bf16"): (1.1e-2, 1.5e-2), ("burgers_L2", "bf16x3"): (1.1e-2, 1.5e-2),
+    ("allen_cahn_L3", "bf16"): (1.3e-2, 6e-3), ("allen_cahn_L3", "bf16x3"): (1.3e-2, 6e-3),
+    ("ks_w64", "bf16"): (2.6e-2, 3e-2), ("ks_w64", "bf16x3"): (2.1e-2, 2.4e-2),
+    ("ns_psi_w128", "bf16"): (1e-2, 9e-3), ("ns_psi_w128", "bf16x3"): (1e-2, 9e-3),
+    ("helmholtz_w256", "bf16"): (7e-3, 7e-3),
+    ("ns_uvp_w64", "bf16"): (6e-2, 6e-2), ("ns_uvp_w64", "bf16x3"): (6e-2, 6e-2),
+}
+# per-channel bounds of test_tc_per_channel_errors by derivative order
+CHANNEL_TOL = {"bf16": {0: 9e-2, 1: 9e-2, 2: 3e-2, 3: 3.5e-2},
+               # the split products lower the third-order channels: their own, tighter bound
+               "bf16x3": {0: 9e-2, 1: 9e-2, 2: 3e-2, 3: 2.6e-2}}
 
 
 def _setup(fam, coefs, widths, domain, N, seed=0):
@@ -71,7 +84,7 @@ def test_tc_matches_oracle(name, fam, coefs, widths, domain, N, prec):
     el = abs(float(loss) - L) / abs(L)
     print("%s %s: residual %.3e gradient %.3e loss %.3e (P=%d, grid=%d)" % (
         name, prec, er, eg, el, plan.info()["tile_points"], plan.info()["grid_ctas"]))
-    tr, tg = TOL[prec]
+    tr, tg = TOL[(name, prec)]
     assert er <= tr and eg <= tg and el <= 2 * tr
     # the forward of the backward pass is the forward pass: identical residuals
     assert torch.equal(r, r_b)
@@ -107,7 +120,8 @@ def test_tc_per_channel_errors():
         print("psi_%s: bf16 %.2e  bf16x3 %.2e  fp32 %.2e" % ("".join(map(str, al)), errs[("bf16", al)],
                                                             errs[("bf16x3", al)], errs[("fp32", al)]))
         assert errs[("fp32", al)] < 1e-5
-        assert errs[("bf16", al)] < 0.1
+        for f in ("bf16", "bf16x3"):
+            assert errs[(f, al)] <= CHANNEL_TOL[f][sum(al)], (f, al)
     top = [al for al in chans if sum(al) == 3]
     # split precision on the third-order channels lowers their error
     assert np.mean([errs[("bf16x3", al)] for al in top]) <= np.mean([errs[("bf16", al)] for al in top])

@@ -213,7 +213,7 @@ def _analytic_jets(sp, syms, exprs, needed, X):
     return out
 
 
-@pytest.mark.parametrize("case", ["burgers", "allen_cahn", "ks", "helmholtz", "ns_psi"])
+@pytest.mark.parametrize("case", ["burgers", "allen_cahn", "ks", "helmholtz", "ns_psi", "ns_uvp"])
 def test_manufactured_solutions(case):
     sp = pytest.importorskip("sympy")
     g = _rng(21)
@@ -242,6 +242,17 @@ def test_manufactured_solutions(case):
         u = sp.sin(sp.pi * x) * sp.sin(sp.pi * y) * sp.sin(sp.pi * z)
         fam, syms, exprs = R.helmholtz(4 * math.pi), (x, y, z), [u]
         X = g.uniform(-1, 1, (50, 3))
+    elif case == "ns_uvp":
+        # Kovasznay flow (Kovasznay 1948): an exact steady solution of the
+        # incompressible Navier-Stokes equations at Reynolds number Re
+        x, y = sp.symbols("x y")
+        Re = 100
+        lam = sp.Rational(Re, 2) - sp.sqrt(sp.Rational(Re * Re, 4) + 4 * sp.pi ** 2)
+        u = 1 - sp.exp(lam * x) * sp.cos(2 * sp.pi * y)
+        v = lam / (2 * sp.pi) * sp.exp(lam * x) * sp.sin(2 * sp.pi * y)
+        p = (1 - sp.exp(2 * lam * x)) / 2
+        fam, syms, exprs = R.navier_stokes_uvp(Re), (x, y), [u, v, p]
+        X = np.column_stack([g.uniform(-0.5, 1.0, 50), g.uniform(-0.5, 1.5, 50)])
     else:
         x, y, t = sp.symbols("x y t")
         nu = 0.01
@@ -299,6 +310,7 @@ FAMS = [
     ("allen_cahn", lambda: R.allen_cahn(1e-4, 5.0), [2, 4, 3, 1]),
     ("helmholtz", lambda: R.helmholtz(4 * math.pi), [3, 4, 4, 1]),
     ("ns_psi", lambda: R.navier_stokes_psi(0.01), [3, 4, 3, 2]),
+    ("ns_uvp", lambda: R.navier_stokes_uvp(100.0), [2, 4, 4, 3]),
 ]
 
 
@@ -371,6 +383,13 @@ def _torch_nested(fam_name, coefs, layers, X):
         ux = D(u, 0)
         uxx = D(ux, 0)
         res = [D(u, 1) + u * ux + uxx + D(D(uxx, 0), 0)]
+    elif fam_name == "ns_uvp":
+        uu, vv, p = h[:, 0], h[:, 1], h[:, 2]
+        Re = coefs["Re"]
+        rc = D(uu, 0) + D(vv, 1)
+        ru = uu * D(uu, 0) + vv * D(uu, 1) + D(p, 0) - (D(uu, 0, 0) + D(uu, 1, 1)) / Re
+        rv = uu * D(vv, 0) + vv * D(vv, 1) + D(p, 1) - (D(vv, 0, 0) + D(vv, 1, 1)) / Re
+        res = [rc, ru, rv]
     else:
         psi, p = h[:, 0], h[:, 1]
         nu = coefs["nu"]
@@ -389,6 +408,7 @@ def _torch_nested(fam_name, coefs, layers, X):
     ("burgers", dict(nu=0.01 / math.pi), [2, 20, 20, 20, 20, 1]),
     ("ks", dict(c1=1.0, c2=1.0, c4=1.0), [2, 16, 16, 16, 1]),
     ("ns_psi", dict(nu=0.01), [3, 12, 12, 12, 2]),
+    ("ns_uvp", dict(Re=100.0), [2, 16, 16, 16, 3]),
 ])
 def test_agrees_with_torch_nested_autograd(fam_name, coefs, widths):
     layers = wl.xavier_layers(widths, 1, bias_std=0.1)

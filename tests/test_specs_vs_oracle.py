@@ -19,6 +19,7 @@ CASES = [
     ("allen_cahn", dict(eps=1e-4, k=5.0)),
     ("helmholtz", dict(k=4 * math.pi)),
     ("ns_psi", dict(nu=0.01)),
+    ("ns_uvp", dict(Re=100.0)),
 ]
 
 
