@@ -38,8 +38,12 @@ TOL = {
     ("ks_w64", "bf16"): (2.6e-2, 3e-2), ("ks_w64", "bf16x3"): (2.1e-2, 2.4e-2),
     ("ns_psi_w128", "bf16"): (1e-2, 9e-3), ("ns_psi_w128", "bf16x3"): (1e-2, 9e-3),
     ("helmholtz_w256", "bf16"): (7e-3, 7e-3),
-    ("ns_uvp_w64", "bf16"): (6e-2, 6e-2), ("ns_uvp_w64", "bf16x3"): (6e-2, 6e-2),
+    ("ns_uvp_w64", "bf16"): (1.5e-2, 8.5e-3), ("ns_uvp_w64", "bf16x3"): (1.5e-2, 8.5e-3),
 }
+# the oracle comparison inside the consistency tests below (store = per-tile,
+# two CTAs = one, packed tiles), whose shapes are not in TOL: the largest bound
+# of TOL
+TOL_ANY = {"bf16": (3e-2, 3e-2), "bf16x3": (3e-2, 3e-2)}
 # per-channel bounds of test_tc_per_channel_errors by derivative order
 CHANNEL_TOL = {"bf16": {0: 9e-2, 1: 9e-2, 2: 3e-2, 3: 3.5e-2},
                # the split products lower the third-order channels: their own, tighter bound
@@ -188,7 +192,7 @@ def test_tc_store_mode_weight_gradient(name, fam, coefs, widths, domain, N, prec
     assert rel_l2(g2.cpu().numpy(), g1.cpu().numpy()) < 1e-12
     assert abs(float(l1) - float(l2)) <= 1e-13 * abs(float(l1))
     assert abs(float(l1) - float(l0)) <= 1e-12 * abs(float(l0))
-    assert rel_l2(g1.cpu().numpy(), g_ref) < TOL[prec][1]
+    assert rel_l2(g1.cpu().numpy(), g_ref) < TOL_ANY[prec][1]
     m = torch.zeros_like(p)
     v = torch.zeros_like(p)
     stored.train_step(p.clone(), m, v, 1, 1e-3, x, s)
@@ -225,8 +229,8 @@ def test_tc_two_ctas_per_sm(name, fam, coefs, widths, domain, N, prec, tile):
     assert torch.equal(r1, r2)
     assert abs(float(l1) - float(l2)) <= 1e-12 * abs(float(l1))
     assert rel_l2(g2.cpu().numpy(), g1.cpu().numpy()) < 1e-5
-    assert rel_l2(r2.cpu().numpy(), r_ref) < TOL[prec][0]
-    assert rel_l2(g2.cpu().numpy(), g_ref) < TOL[prec][1]
+    assert rel_l2(r2.cpu().numpy(), r_ref) < TOL_ANY[prec][0]
+    assert rel_l2(g2.cpu().numpy(), g_ref) < TOL_ANY[prec][1]
 
 
 def test_tc_two_ctas_rejects_wide_layers():
@@ -258,7 +262,7 @@ def test_tc_packed_subtiles_any_tile(width, tiles):
         g, _, _ = plan.backward(p, x)
         torch.cuda.synchronize()
         outs.append((r.cpu().numpy(), g.cpu().numpy()))
-        assert rel_l2(outs[-1][0], r_ref) < TOL["bf16"][0] and rel_l2(outs[-1][1], g_ref) < TOL["bf16"][1]
+        assert rel_l2(outs[-1][0], r_ref) < TOL_ANY["bf16"][0] and rel_l2(outs[-1][1], g_ref) < TOL_ANY["bf16"][1]
     for r, g in outs[1:]:
         assert rel_l2(r, outs[0][0]) < 1e-5 and rel_l2(g, outs[0][1]) < 1e-4
     # a tile that is not a whole number of sub-tiles of 8 points is refused
