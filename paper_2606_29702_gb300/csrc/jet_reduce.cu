@@ -60,12 +60,17 @@ __global__ void __launch_bounds__(32 * kRedWarps) reduce_kernel(const __grid_con
   __shared__ double part[kRedWarps][32];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int gc = J.grad_chunks > 0 ? J.grad_chunks : J.n_chunks;
-  double bc1 = 1.0, bc2 = 1.0;
+  // bias corrections: one thread per block (FP64 pow is slow on this GPU)
+  __shared__ double bc_s[2];
   if (ADAM) {
-    const long long t = ac.step_ctr ? *ac.step_ctr + 1 : ac.step;
-    bc1 = 1.0 - pow(ac.beta1, (double)t);
-    bc2 = 1.0 - pow(ac.beta2, (double)t);
+    if (threadIdx.x == 0) {
+      const long long t = ac.step_ctr ? *ac.step_ctr + 1 : ac.step;
+      bc_s[0] = 1.0 - pow(ac.beta1, (double)t);
+      bc_s[1] = 1.0 - pow(ac.beta2, (double)t);
+    }
+    __syncthreads();
   }
+  const double bc1 = ADAM ? bc_s[0] : 1.0, bc2 = ADAM ? bc_s[1] : 1.0;
   const float bc1_f = (float)bc1, bc2_f = (float)bc2;
   for (long long p0 = (long long)blockIdx.x * 32; p0 < J.n_params; p0 += (long long)gridDim.x * 32) {
     const long long p = p0 + lane;

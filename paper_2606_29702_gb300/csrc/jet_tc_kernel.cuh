@@ -154,7 +154,8 @@ struct TcTile {
   static constexpr int PPF = C >= 7 ? 2 : 4;   // points per epilogue pass (forward)
   static constexpr int PPB = C >= 5 ? 2 : 4;   // points per epilogue pass (adjoint)
 
-  const TcInst& I;
+  const TcInst& I;      // the work item's descriptor, copied to shared memory
+  const TcInst* Imap;   // the same descriptor in param or global space: its tensor maps serve TMA
   unsigned char* sm;
   uint64_t* bar_tma;
   uint64_t* bar_mma;
@@ -200,8 +201,8 @@ struct TcTile {
     const uint32_t box = 64u * R * 2u;
     tc::mbar_arrive_expect_tx(bar_tma, box * nck * (I.split3 ? 2u : 1u));
     for (int kc = 0; kc < nck; ++kc) {
-      tc::tma_load_3d(sm + I.o_w + kc * box, &I.wmap, bar_tma, kc * 64, 0, l - 2);
-      if (I.split3) tc::tma_load_3d(sm + I.o_wlo + kc * box, &I.wlomap, bar_tma, kc * 64, 0, l - 2);
+      tc::tma_load_3d(sm + I.o_w + kc * box, &Imap->wmap, bar_tma, kc * 64, 0, l - 2);
+      if (I.split3) tc::tma_load_3d(sm + I.o_wlo + kc * box, &Imap->wlomap, bar_tma, kc * 64, 0, l - 2);
     }
   }
 
@@ -209,7 +210,7 @@ struct TcTile {
     const int nck = (I.w + 63) / 64;
     const uint32_t box = 64u * 128u * 2u;
     tc::mbar_arrive_expect_tx(bar_tma, box * nck);
-    for (int kc = 0; kc < nck; ++kc) tc::tma_load_2d(sm + I.o_w + kc * box, &I.wlmap, bar_tma, kc * 64, 0);
+    for (int kc = 0; kc < nck; ++kc) tc::tma_load_2d(sm + I.o_w + kc * box, &Imap->wlmap, bar_tma, kc * 64, 0);
   }
 
   long long cur_tile = 0;
@@ -221,6 +222,17 @@ struct TcTile {
     if (I.wstore) return I.wstore + cur_tile * I.wstore_tile_stride + off;
     return I.scratch + (long long)blockIdx.x * I.scratch_stride + off;
   }
+  // layer-input copies: the per-CTA scratch slot is rewritten every tile and
+  // stays in L2 (evict_last); the store streams through it (default policy)
+  __device__ void scratch_out(unsigned char* dst, const unsigned char* src, uint32_t bytes) const {
+    if (I.wstore) tc::bulk_s2g(dst, src, bytes);
+    else tc::bulk_s2g_hint(dst, src, bytes, tc::policy_evict_last());
+  }
+  __device__ void scratch_in(unsigned char* dst, const unsigned char* src, uint32_t bytes) const {
+    if (I.wstore) tc::bulk_g2s(dst, src, bytes, bar_ld);
+    else tc::bulk_g2s_hint(dst, src, bytes, bar_ld, tc::policy_evict_last());
+  }
+
   // adjoint Zbar^l (l = 2..L-1) of the tile in the store
   __device__ unsigned char* zslot(int l) const {
     return I.wstore + cur_tile * I.wstore_tile_stride + (long long)(I.L - 2) * (I.act_bytes + I.alo_bytes) +
@@ -479,11 +491,21 @@ struct TcTile {
     }
     __syncthreads();
     for (int n = tid; n < nvalid; n += nthr) {
+      const int nres = I.n_res;
       float r[kMaxRes];
-      for (int c = 0; c < I.n_res; ++c) r[c] = I.source ? -I.source[(n0 + n) * I.n_res + c] : 0.f;
-      for (int m = 0; m < nt; ++m) r[I.terms[m].comp] += prodm[m * P + n];
-      for (int c = 0; c < I.n_res; ++c) {
-        if (I.r_out) I.r_out[(n0 + n) * I.n_res + c] = r[c];
+#pragma unroll
+      for (int c = 0; c < kMaxRes; ++c) r[c] = (c < nres && I.source) ? -I.source[(n0 + n) * nres + c] : 0.f;
+      for (int m = 0; m < nt; ++m) {
+        const int cm = I.terms[m].comp;
+        const float v = prodm[m * P + n];
+#pragma unroll
+        for (int c = 0; c < kMaxRes; ++c)
+          if (c == cm) r[c] += v;
+      }
+#pragma unroll
+      for (int c = 0; c < kMaxRes; ++c) {
+        if (c >= nres) break;
+        if (I.r_out) I.r_out[(n0 + n) * nres + c] = r[c];
         loss += (double)r[c] * (double)r[c];
         rg[c * P + n] = two_over_n * r[c];
       }
@@ -521,6 +543,7 @@ struct TcTile {
       const int r = h * 128 + ul;
       if (r >= I.w) continue;
       const int sub = r / I.wu;
+      const int nout = I.n_out;
       float acc[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
       for (int c = wg; c < C; c += nwg)
         for (int q8 = 0; q8 < Pc; q8 += 8) {
@@ -528,11 +551,16 @@ struct TcTile {
           const uint4 raw = *reinterpret_cast<const uint4*>(ACT(a_buf) + tc::swz_off(r, col, R));
           const __nv_bfloat16* bv = reinterpret_cast<const __nv_bfloat16*>(&raw);
           const float* ubc = ub + c * P + sub * Pc + q8;
-          for (int o = 0; o < I.n_out; ++o)
+#pragma unroll
+          for (int o = 0; o < kMaxOut; ++o) {
+            if (o >= nout) break;
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[o] = fmaf(__bfloat162float(bv[j]), ubc[o * C * P + j], acc[o]);
+          }
         }
-      for (int o = 0; o < I.n_out; ++o) PART(wg, o, r) = acc[o];
+#pragma unroll
+      for (int o = 0; o < kMaxOut; ++o)
+        if (o < nout) PART(wg, o, r) = acc[o];
     }
   }
 
@@ -581,9 +609,13 @@ struct TcTile {
       if (h * 128 + q * 32 >= I.w) continue;
       const int sub = r / I.wu, u = r - sub * I.wu;
       const float bu = I.params[I.off_b[l - 1] + u];
+      const int nout = I.n_out;
       float wl[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
-      if (abar_from_ub)
-        for (int o = 0; o < I.n_out; ++o) wl[o] = I.params[I.off_W[I.L - 1] + (long long)o * I.wu + u];
+      if (abar_from_ub) {
+#pragma unroll
+        for (int o = 0; o < kMaxOut; ++o)
+          if (o < nout) wl[o] = I.params[I.off_W[I.L - 1] + (long long)o * I.wu + u];
+      }
       float gb = 0.f;
       for (int g = wg * PPB; g < Pc; g += nwg * PPB) {
         float zv[C][PPB], abv[C][PPB];
@@ -600,7 +632,9 @@ struct TcTile {
 #pragma unroll
             for (int j = 0; j < PPB; ++j) {
               float s = 0.f;
-              for (int o = 0; o < I.n_out; ++o) s = fmaf(wl[o], ub[(o * C + c) * P + sub * Pc + g + j], s);
+#pragma unroll
+              for (int o = 0; o < kMaxOut; ++o)
+                if (o < nout) s = fmaf(wl[o], ub[(o * C + c) * P + sub * Pc + g + j], s);
               abv[c][j] = s;
             }
         }
@@ -650,13 +684,13 @@ struct TcTile {
 
   // TMEM columns of lane row (8, from taddr) -> accumulator columns k0 .. k0+7
   // of row u in the [k / 4][u][4] block at acc
-  __device__ void acc8(float* acc, int u, int k0, uint32_t taddr) const {
+  __device__ void acc8(float* acc, int u, int k0, uint32_t taddr, uint64_t pol) const {
     float v[8];
     tc::tmem_ld8(taddr, v);
     tc::tmem_wait_ld();
     const int wu = I.wu;
-    red_add_v4(acc + ((long long)(k0 / 4) * wu + u) * 4, v[0], v[1], v[2], v[3]);
-    red_add_v4(acc + ((long long)(k0 / 4 + 1) * wu + u) * 4, v[4], v[5], v[6], v[7]);
+    tc::red_add_v4_hint(acc + ((long long)(k0 / 4) * wu + u) * 4, v[0], v[1], v[2], v[3], pol);
+    tc::red_add_v4_hint(acc + ((long long)(k0 / 4 + 1) * wu + u) * 4, v[4], v[5], v[6], v[7], pol);
   }
 
   // D[R0] (weight-gradient columns nb*NB .. of layer l) -> accumulator.  With
@@ -666,15 +700,18 @@ struct TcTile {
   __device__ void acc_wgrad(int l, int nb, int NB) {
     float* acc = wacc(l);
     const int wu = I.wu;
+    const uint64_t pol = tc::policy_evict_last();
     if (I.G > 1) {  // packed plans have H == 1
       const int sub = ul / wu, j = ul - sub * wu;
       float* a = acc + (long long)sub * wu * wu;
-      for (int k0 = wg * 8; k0 < wu; k0 += nwg * 8) acc8(a, j, k0, R0(0) + lane_base() + (uint32_t)(sub * wu + k0));
+      for (int k0 = wg * 8; k0 < wu; k0 += nwg * 8)
+        acc8(a, j, k0, R0(0) + lane_base() + (uint32_t)(sub * wu + k0), pol);
       return;
     }
     for (int h = 0; h < I.H; ++h) {
       if (h * 128 + q * 32 >= I.w) continue;  // warp-uniform
-      for (int k0 = wg * 8; k0 < NB; k0 += nwg * 8) acc8(acc, h * 128 + ul, nb * NB + k0, R0(h) + lane_base() + (uint32_t)k0);
+      for (int k0 = wg * 8; k0 < NB; k0 += nwg * 8)
+        acc8(acc, h * 128 + ul, nb * NB + k0, R0(h) + lane_base() + (uint32_t)k0, pol);
     }
   }
 
@@ -719,9 +756,13 @@ struct TcTile {
 #pragma unroll
       for (int i = 0; i < d; ++i) w1[i] = Pm[I.off_W[0] + u * d + i];
       const float b1 = Pm[I.off_b[0] + u];
+      const int nout = I.n_out;
       float wl[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
-      if (abar_from_ub)
-        for (int o = 0; o < I.n_out; ++o) wl[o] = Pm[I.off_W[I.L - 1] + (long long)o * I.wu + u];
+      if (abar_from_ub) {
+#pragma unroll
+        for (int o = 0; o < kMaxOut; ++o)
+          if (o < nout) wl[o] = Pm[I.off_W[I.L - 1] + (long long)o * I.wu + u];
+      }
       const float* xs = XS() + sub * Pc * d;
       float gw[d], gb = 0.f;
 #pragma unroll
@@ -738,7 +779,9 @@ struct TcTile {
 #pragma unroll
             for (int j = 0; j < PPB; ++j) {
               float s = 0.f;
-              for (int o = 0; o < I.n_out; ++o) s = fmaf(wl[o], ub[(o * C + c) * P + sub * Pc + g + j], s);
+#pragma unroll
+              for (int o = 0; o < kMaxOut; ++o)
+                if (o < nout) s = fmaf(wl[o], ub[(o * C + c) * P + sub * Pc + g + j], s);
               abv[c][j] = s;
             }
         }
@@ -820,8 +863,8 @@ struct TcTile {
     // scratch keeps A^l for l <= L-3 (A^{L-2} stays in shared memory for the
     // backward); the store keeps A^{L-2} as well, for the weight-gradient GEMM
     if (tid == 0 && bwd && 1 <= last_a && !*abort_f) {
-      tc::bulk_s2g(slot(1), ACT(0), (uint32_t)I.act_bytes);
-      if (I.split3) tc::bulk_s2g(slot(1) + I.act_bytes, ALO(0), (uint32_t)I.alo_bytes);
+      scratch_out(slot(1), ACT(0), (uint32_t)I.act_bytes);
+      if (I.split3) scratch_out(slot(1) + I.act_bytes, ALO(0), (uint32_t)I.alo_bytes);
       tc::bulk_commit();
     }
     int cur = 0;
@@ -843,8 +886,8 @@ struct TcTile {
       tc::fence_proxy_async_smem();
       sync();
       if (tid == 0 && bwd && l <= last_a) {
-        tc::bulk_s2g(slot(l), ACT(cur ^ 1), (uint32_t)I.act_bytes);
-        if (I.split3) tc::bulk_s2g(slot(l) + I.act_bytes, ALO(cur ^ 1), (uint32_t)I.alo_bytes);
+        scratch_out(slot(l), ACT(cur ^ 1), (uint32_t)I.act_bytes);
+        if (I.split3) scratch_out(slot(l) + I.act_bytes, ALO(cur ^ 1), (uint32_t)I.alo_bytes);
         tc::bulk_commit();
       }
       cur ^= 1;
@@ -878,8 +921,8 @@ struct TcTile {
     auto request_reload = [&](int l) {
       tc::bulk_wait0();
       tc::mbar_arrive_expect_tx(bar_ld, (uint32_t)(I.act_bytes + (I.split3 ? I.alo_bytes : 0)));
-      tc::bulk_g2s(ACT(ain), slot(l - 1), (uint32_t)I.act_bytes, bar_ld);
-      if (I.split3) tc::bulk_g2s(ALO(ain), slot(l - 1) + I.act_bytes, (uint32_t)I.alo_bytes, bar_ld);
+      scratch_in(ACT(ain), slot(l - 1), (uint32_t)I.act_bytes);
+      if (I.split3) scratch_in(ALO(ain), slot(l - 1) + I.act_bytes, (uint32_t)I.alo_bytes);
       load_hidden_w(l);
     };
     for (int l = L - 1; l >= 2; --l) {
@@ -955,6 +998,9 @@ template <class Cls>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant__ TcArgs args) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t bars[3];
+  // the running work item's descriptor: every epilogue reads its fields, and
+  // shared-memory loads keep those reads off the global/param path
+  __shared__ TcInst inst_s;
   __shared__ uint32_t tmem_s;
   __shared__ volatile int abort_s;
   __shared__ double red_s[kTcThreads / 32];
@@ -980,7 +1026,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
   for (int k = blockIdx.x; k < args.n_items && !abort_s; k += gridDim.x) {
     const int item = args.item_inst ? args.item_inst[k] : k;
     const int ii = args.insts ? args.item_inst[args.n_items + item] : 0;
-    const TcInst& I = args.insts ? args.insts[ii] : args.inst0;
+    const TcInst& Ig = args.insts ? args.insts[ii] : args.inst0;
+    if (ii != prev_inst) {
+      // the previous item's readers of inst_s passed the barrier at its end
+      const uint4* src = reinterpret_cast<const uint4*>(&Ig);
+      uint4* dst = reinterpret_cast<uint4*>(&inst_s);
+      for (int i = tid; i < (int)(sizeof(TcInst) / 16); i += nthr) dst[i] = src[i];
+      __syncthreads();
+    }
+    const TcInst& I = inst_s;
     const int chunk = item - I.chunk_base;
     if (ii != prev_inst) {
       // zero both activation buffers (and split buffers) once per instance:
@@ -996,14 +1050,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
           reinterpret_cast<uint4*>(sm + I.o_alo1)[i] = z4;
         }
       if (tid == 0) {
-        tc::prefetch_tensormap(&I.wmap);
-        tc::prefetch_tensormap(&I.wlmap);
+        tc::prefetch_tensormap(&Ig.wmap);
+        tc::prefetch_tensormap(&Ig.wlmap);
       }
       tc::fence_proxy_async_smem();
       __syncthreads();
       prev_inst = ii;
     }
     TcTile<Cls> T{I,
+                  &Ig,
                   sm,
                   &bars[0],
                   &bars[1],
