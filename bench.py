@@ -55,6 +55,8 @@ SIDE = [("helmholtz_3x256x8", "bf16", "store"), ("helmholtz_3x256x8", "bf16", "t
         ("ns_psi_3x128x6", "bf16", "tile"), ("ns_psi_3x128x6", "bf16x3", "tile"), ("ns_psi_3x128x6", "fp32", "tile"),
         ("ks_2x64x5", "fp32", "tile"), ("ks_2x64x5", "bf16", "tile"), ("ks_2x64x5", "bf16x3", "tile"),
         ("burgers_2x20x4", "fp64", "tile"),
+        ("burgers_loss_2x64x6", "fp32", "tile"), ("burgers_loss_2x64x6", "bf16", "tile"),
+        ("cavity_loss_2x64x6", "fp32", "tile"), ("cavity_loss_2x64x6", "bf16", "tile"),
         ("ensemble_64", "bf16", "tile"), ("ensemble_64", "fp32", "tile")]
 
 
@@ -568,9 +570,57 @@ def run_ensemble(args, rank, ws, local):
         print(json.dumps(out))
 
 
+def time_loss_form(name, form, steps, warmup, flush):
+    """Train steps of a composite-loss workload (Sec. 3.1.1: IC, BC and PDE
+    terms over their own points, all points batched into one evaluation)."""
+    import torch
+    from paper_2606_29702_gb300 import jet, specs
+    from paper_2606_29702_gb300 import workloads as wl
+    spec, X, counts, src, layers = wl.loss_workload(name)
+    terms = specs.burgers_loss_terms(**spec["coefs"]) if spec["kind"] == "burgers" else \
+        specs.cavity_loss_terms(**spec["coefs"])
+    plan = jet.LossPlan(terms, spec["widths"], form)
+    plan.set_term_points(counts)
+    dev = torch.device("cuda")
+    p = torch.tensor(wl.pack(layers), dtype=plan.dtype, device=dev)
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    x = torch.tensor(X, dtype=plan.dtype, device=dev)
+    s = torch.tensor(src, dtype=plan.dtype, device=dev)
+    loss = torch.empty((), dtype=torch.float64, device=dev)
+    for k in range(warmup):
+        plan.train_step(p, m, v, k + 1, 1e-3, x, s, loss)
+    torch.cuda.synchronize()
+    plan.profile(True)
+    plan.profile_read()
+    evs = []
+    for k in range(steps):
+        flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.train_step(p, m, v, warmup + k + 1, 1e-3, x, s, loss)
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    n, kms = plan.profile_read()
+    info = plan.info()
+    plan.close()
+    return {"ms_per_step": ms, "value": X.shape[0] / (ms * 1e-3), "kernel_ms": kms / max(n, 1), "info": info,
+            "points": X.shape[0], "counts": counts, "widths": spec["widths"]}
+
+
 def side_entry(name, form, schedule, steps, flush, peaks, peak_kind):
     """One named workload timed beside the headline (rank 0, one replica)."""
     from paper_2606_29702_gb300 import workloads as wl
+    if name in wl.LOSS_WORKLOADS:
+        r = time_loss_form(name, form, steps, 3, flush)
+        fpp = flops_per_point(r["widths"], r["info"]["n_channels"])
+        return {"value": r["value"], "ms_per_step": r["ms_per_step"], "kernel_ms": r["kernel_ms"],
+                "points": r["points"], "term_points": r["counts"], "form": form,
+                "tile_points": r["info"]["tile_points"], "channels": r["info"]["n_channels"],
+                "step": "jet_train_step on the composite loss (all points batched)",
+                "roofline": roofline(form, fpp * r["points"], r["kernel_ms"], peaks, peak_kind, None)}
     if name == "ensemble_64":
         r = time_ensemble(form, steps, 3, e2e=False)
         return {"value": r["value"], "ms_per_step": r["ms_per_step"], "points": r["n_pts"], "form": form,

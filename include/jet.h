@@ -173,6 +173,58 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
                            const int32_t* widths, int32_t n_needed, const jet_chan* needed,
                            jet_precision prec, size_t mem_budget_bytes, int32_t flags);
 
+/*
+ * Composite PINN loss with all-points batching (Sec. 3.1.1): the training
+ * loss of the paper's Burgers and lid-driven cavity cases sums weighted terms
+ * -- initial-condition, boundary-condition and PDE-residual terms -- each
+ * over its own point set, and the network (with its derivative channels) is
+ * evaluated once on all points concatenated, the outputs split afterwards:
+ *
+ *   L = sum_g weight_g * (1 / M_g) * sum_{residuals m of term g} sum_c r_{g,c,m}^2
+ *
+ * Term g owns a contiguous block of the concatenated points, in term order
+ * (counts from jet_plan_set_term_points).  A plain term has one residual per
+ * point (M_g = its points).  A paired term owns its points as consecutive
+ * pairs (a, b) and has one residual per pair (M_g = half its points), whose
+ * monomial factors read the jets at a, or at b when their jet_chan.out
+ * carries JET_PAIR_SECOND: e.g. the periodic boundary conditions
+ * u(0, t) - u(1, t) and u_x(0, t) - u_x(1, t).  A paired term must start at
+ * an even point index.
+ */
+#define JET_PAIR_SECOND 0x100 /* jet_chan.out flag: factor read at the pair's second point */
+
+typedef struct {
+  const jet_residual_spec* spec; /* the term's residual (its own source flag) */
+  double weight;                 /* weight_g >= 0 */
+  int32_t paired;                /* 1: one residual per consecutive pair of points */
+} jet_loss_term;
+
+/*
+ * Create a plan for a composite loss of n_terms (1..4) terms on one network
+ * shape.  The carried channel set is the closure of `needed`, which must
+ * cover every term's multi-indices (JET_FLAG_AUTO_CLOSE closes it); all other
+ * arguments as jet_plan_create.  The plan's n_res is the largest of the
+ * terms'.  Before its compute calls, jet_plan_set_term_points gives the point
+ * count of every term; then every call takes X = the terms' points
+ * concatenated in term order with N = their sum, source [N][n_res] (rows of
+ * terms whose spec has no source are ignored) if any term has one, and
+ * writes r_out [N][n_res] with each term's components at its residual points
+ * (zeros at the second points of pairs and in components a term lacks).
+ * loss_out is L above.  Batches accept such plans.
+ */
+jet_status jet_plan_create_loss(jet_plan_t* out, int32_t n_terms, const jet_loss_term* terms, int32_t d_in,
+                                int32_t n_layers, const int32_t* widths, int32_t n_needed, const jet_chan* needed,
+                                jet_precision prec, size_t mem_budget_bytes, int32_t flags);
+
+/*
+ * Point counts of a composite-loss plan's terms (host array [n_terms]) for
+ * its next calls.  JET_ERR_INVALID for a plan with one residual, a negative
+ * count, or a paired term that would not start at an even point index or
+ * holds an odd number of points.  Host-side state only: a call captured in a
+ * CUDA graph keeps the counts it was captured with.
+ */
+jet_status jet_plan_set_term_points(jet_plan_t plan, const int64_t* counts);
+
 jet_status jet_plan_get_info(jet_plan_t plan, jet_plan_info* info);
 
 /*

@@ -176,12 +176,20 @@ const char* jet_last_error(void) { return g_err.c_str(); }
 
 const char* jet_version(void) { return "libjet 0.1 (sm_103a)"; }
 
-jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32_t d_in, int32_t n_layers,
-                           const int32_t* widths, int32_t n_needed, const jet_chan* needed, jet_precision prec,
-                           size_t mem_budget_bytes, int32_t flags) {
+}  // extern "C"
+
+// Plan creation for one residual (n_specs = 1, grouped = false: the loss is
+// the mean over all N points) or for a composite loss of n_specs terms, each
+// over its own block of points (grouped = true).
+static jet_status plan_create(jet_plan_t* out, int n_specs, const jet_residual_spec* const* specs,
+                              const double* weights, const int32_t* paired, bool grouped, int32_t d_in,
+                              int32_t n_layers, const int32_t* widths, int32_t n_needed, const jet_chan* needed,
+                              jet_precision prec, size_t mem_budget_bytes, int32_t flags) {
   if (!out) return fail(JET_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (!spec || !widths || (n_needed > 0 && !needed)) return fail(JET_ERR_INVALID, "NULL spec, widths or needed");
+  if (!specs || !widths || (n_needed > 0 && !needed)) return fail(JET_ERR_INVALID, "NULL spec, widths or needed");
+  for (int g = 0; g < n_specs; ++g)
+    if (!specs[g]) return fail(JET_ERR_INVALID, "NULL residual spec of loss term %d", g);
   if (d_in < 1 || d_in > 3) return fail(JET_ERR_INVALID, "d_in must be 1..3 (got %d)", d_in);
   if (n_layers < 2 || n_layers > kMaxLayers) return fail(JET_ERR_INVALID, "n_layers must be 2..%d", kMaxLayers);
   if (widths[0] != d_in) return fail(JET_ERR_INVALID, "widths[0] (%d) != d_in (%d)", widths[0], d_in);
@@ -191,8 +199,11 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
     if (widths[l] < 4 || widths[l] > 256 || widths[l] % 4)
       return fail(JET_ERR_UNSUPPORTED, "hidden width %d: must be a multiple of 4 in [4, 256]", widths[l]);
   if (prec < JET_FP64 || prec > JET_BF16X3) return fail(JET_ERR_INVALID, "unknown precision %d", (int)prec);
-  if (spec->n_res < 1 || spec->n_res > kMaxRes || !spec->n_mono || !spec->mono)
-    return fail(JET_ERR_INVALID, "residual spec: n_res must be 1..%d with n_mono and mono set", kMaxRes);
+  for (int g = 0; g < n_specs; ++g) {
+    const jet_residual_spec* spec = specs[g];
+    if (spec->n_res < 1 || spec->n_res > kMaxRes || !spec->n_mono || !spec->mono)
+      return fail(JET_ERR_INVALID, "residual spec: n_res must be 1..%d with n_mono and mono set", kMaxRes);
+  }
 
   // ---- channel closure (Sec. 2.2: required states plus their lower-order chain)
   std::set<Alpha> need;
@@ -211,24 +222,34 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
                 need.size(), closure.size());
   // every spec factor must be carried
   int n_terms = 0;
-  for (int c = 0; c < spec->n_res; ++c) {
-    if (spec->n_mono[c] < 0 || (spec->n_mono[c] > 0 && !spec->mono[c]))
-      return fail(JET_ERR_INVALID, "residual component %d: bad monomial list", c);
-    n_terms += spec->n_mono[c];
+  for (int g = 0; g < n_specs; ++g) {
+    const jet_residual_spec* spec = specs[g];
+    for (int c = 0; c < spec->n_res; ++c) {
+      if (spec->n_mono[c] < 0 || (spec->n_mono[c] > 0 && !spec->mono[c]))
+        return fail(JET_ERR_INVALID, "residual component %d: bad monomial list", c);
+      n_terms += spec->n_mono[c];
+    }
   }
   if (n_terms > kMaxTerms) return fail(JET_ERR_UNSUPPORTED, "%d monomials > %d", n_terms, kMaxTerms);
-  for (int c = 0; c < spec->n_res; ++c)
-    for (int m = 0; m < spec->n_mono[c]; ++m) {
-      const jet_monomial& mo = spec->mono[c][m];
-      if (mo.n_fac < 0 || mo.n_fac > 4) return fail(JET_ERR_INVALID, "monomial with %d factors", mo.n_fac);
-      for (int f = 0; f < mo.n_fac; ++f) {
-        if (mo.fac[f].out < 0 || mo.fac[f].out >= n_out)
-          return fail(JET_ERR_INVALID, "monomial factor output %d out of range", mo.fac[f].out);
-        Alpha a(d_in);
-        for (int j = 0; j < d_in; ++j) a[j] = mo.fac[f].alpha[j];
-        if (!closure.count(a)) return fail(JET_ERR_INVALID, "residual uses a multi-index that is not in needed");
+  for (int g = 0; g < n_specs; ++g) {
+    const jet_residual_spec* spec = specs[g];
+    for (int c = 0; c < spec->n_res; ++c)
+      for (int m = 0; m < spec->n_mono[c]; ++m) {
+        const jet_monomial& mo = spec->mono[c][m];
+        if (mo.n_fac < 0 || mo.n_fac > 4) return fail(JET_ERR_INVALID, "monomial with %d factors", mo.n_fac);
+        for (int f = 0; f < mo.n_fac; ++f) {
+          const int o = mo.fac[f].out & ~JET_PAIR_SECOND;
+          if ((mo.fac[f].out & JET_PAIR_SECOND) && !(paired && paired[g]))
+            return fail(JET_ERR_INVALID, "JET_PAIR_SECOND in a term that is not paired");
+          if (o < 0 || o >= n_out) return fail(JET_ERR_INVALID, "monomial factor output %d out of range", o);
+          Alpha a(d_in);
+          for (int j = 0; j < d_in; ++j) a[j] = mo.fac[f].alpha[j];
+          for (int j = d_in; j < 4; ++j)
+            if (mo.fac[f].alpha[j]) return fail(JET_ERR_INVALID, "a residual factor differentiates a coordinate >= d_in");
+          if (!closure.count(a)) return fail(JET_ERR_INVALID, "residual uses a multi-index that is not in needed");
+        }
       }
-    }
+  }
   // ---- smallest compiled channel set containing the closure
   int best = -1;
   for (int k = 0; k < kNumClasses; ++k) {
@@ -251,7 +272,8 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
   p->d = d_in;
   p->L = n_layers;
   p->n_out = n_out;
-  p->n_res = spec->n_res;
+  p->n_res = 0;
+  for (int g = 0; g < n_specs; ++g) p->n_res = std::max(p->n_res, (int)specs[g]->n_res);
   p->widths.assign(widths, widths + n_layers + 1);
   p->cls = best;
   p->C = kClassInfo[best].C;
@@ -259,7 +281,8 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
   p->fp64 = prec == JET_FP64;
   p->tc = prec >= JET_TF32;
   p->elem = p->fp64 ? 8 : 4;
-  p->has_source = spec->has_source != 0;
+  p->has_source = false;
+  for (int g = 0; g < n_specs; ++g) p->has_source = p->has_source || specs[g]->has_source != 0;
   auto chan_index = [&](const jet_chan& ch) {
     const ClassInfo& ci = kClassInfo[best];
     for (int c = 0; c < ci.C; ++c) {
@@ -269,17 +292,34 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
     }
     return -1;
   };
-  for (int c = 0; c < spec->n_res; ++c)
-    for (int m = 0; m < spec->n_mono[c]; ++m) {
-      const jet_monomial& mo = spec->mono[c][m];
-      DevTerm t;
-      t.coef = mo.coef;
-      t.comp = c;
-      t.nfac = mo.n_fac;
-      for (int f = 0; f < 4; ++f) t.fac[f] = 0;
-      for (int f = 0; f < mo.n_fac; ++f) t.fac[f] = mo.fac[f].out * p->C + chan_index(mo.fac[f]);
-      p->terms.push_back(t);
-    }
+  for (int g = 0; g < n_specs; ++g) {
+    const jet_residual_spec* spec = specs[g];
+    DevGroup G;
+    memset(&G, 0, sizeof(G));
+    G.t0 = (int)p->terms.size();
+    for (int c = 0; c < spec->n_res; ++c)
+      for (int m = 0; m < spec->n_mono[c]; ++m) {
+        const jet_monomial& mo = spec->mono[c][m];
+        DevTerm t;
+        t.coef = mo.coef;
+        t.comp = c;
+        t.nfac = mo.n_fac;
+        t.pmask = 0;
+        for (int f = 0; f < 4; ++f) t.fac[f] = 0;
+        for (int f = 0; f < mo.n_fac; ++f) {
+          t.fac[f] = (mo.fac[f].out & ~JET_PAIR_SECOND) * p->C + chan_index(mo.fac[f]);
+          if (mo.fac[f].out & JET_PAIR_SECOND) t.pmask |= 1 << f;
+        }
+        p->terms.push_back(t);
+      }
+    G.t1 = (int)p->terms.size();
+    G.n_res = spec->n_res;
+    G.paired = paired && paired[g] ? 1 : 0;
+    G.has_source = spec->has_source != 0;
+    G.scale = weights ? weights[g] : 1.0;  // the term's weight; divided by its residual count per call
+    p->groups.push_back(G);
+  }
+  p->n_groups = grouped ? n_specs : 0;
   long long off = 0;
   for (int l = 0; l < n_layers; ++l) {
     p->off_W.push_back(off);
@@ -359,6 +399,52 @@ jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32
     }
   }
   *out = p;
+  return JET_OK;
+}
+
+extern "C" {
+
+jet_status jet_plan_create(jet_plan_t* out, const jet_residual_spec* spec, int32_t d_in, int32_t n_layers,
+                           const int32_t* widths, int32_t n_needed, const jet_chan* needed, jet_precision prec,
+                           size_t mem_budget_bytes, int32_t flags) {
+  if (!spec) {
+    if (out) *out = nullptr;
+    return fail(JET_ERR_INVALID, "NULL spec, widths or needed");
+  }
+  return plan_create(out, 1, &spec, nullptr, nullptr, false, d_in, n_layers, widths, n_needed, needed, prec,
+                     mem_budget_bytes, flags);
+}
+
+jet_status jet_plan_create_loss(jet_plan_t* out, int32_t n_terms, const jet_loss_term* terms, int32_t d_in,
+                                int32_t n_layers, const int32_t* widths, int32_t n_needed, const jet_chan* needed,
+                                jet_precision prec, size_t mem_budget_bytes, int32_t flags) {
+  if (out) *out = nullptr;
+  if (!terms || n_terms < 1 || n_terms > kMaxGroups)
+    return fail(JET_ERR_INVALID, "a composite loss takes 1..%d terms", kMaxGroups);
+  std::vector<const jet_residual_spec*> specs(n_terms);
+  std::vector<double> weights(n_terms);
+  std::vector<int32_t> paired(n_terms);
+  for (int g = 0; g < n_terms; ++g) {
+    specs[g] = terms[g].spec;
+    weights[g] = terms[g].weight;
+    paired[g] = terms[g].paired ? 1 : 0;
+    if (!(terms[g].weight >= 0.0)) return fail(JET_ERR_INVALID, "loss term %d: weight must be >= 0", g);
+  }
+  return plan_create(out, n_terms, specs.data(), weights.data(), paired.data(), true, d_in, n_layers, widths,
+                     n_needed, needed, prec, mem_budget_bytes, flags);
+}
+
+jet_status jet_plan_set_term_points(jet_plan_t p, const int64_t* counts) {
+  if (!p || !counts) return fail(JET_ERR_INVALID, "NULL plan or counts");
+  if (p->n_groups == 0) return fail(JET_ERR_INVALID, "the plan has one residual over all points (no loss terms)");
+  long long start = 0;
+  for (int g = 0; g < p->n_groups; ++g) {
+    if (counts[g] < 0) return fail(JET_ERR_INVALID, "loss term %d: negative point count", g);
+    if (p->groups[g].paired && ((start | counts[g]) & 1))
+      return fail(JET_ERR_INVALID, "paired loss term %d must start at an even point index and hold whole pairs", g);
+    start += counts[g];
+  }
+  p->group_counts.assign(counts, counts + p->n_groups);
   return JET_OK;
 }
 
@@ -444,6 +530,10 @@ void fill_instance(const jet_plan_s* p, const void* params, const void* X, long 
   I.inv_N = N > 0 ? 1.0 / (double)N : 0.0;
   I.n_terms = (int)p->terms.size();
   for (int m = 0; m < I.n_terms; ++m) I.terms[m] = p->terms[m];
+  if (p->n_groups > 0) {
+    I.inv_N = 1.0;  // each term's mean is in its scale
+    I.n_groups = fill_groups(p, I.groups);
+  }
   I.P = p->P;
   I.pitch = p->pitch;
   I.S = p->S;
@@ -463,6 +553,13 @@ void fill_instance(const jet_plan_s* p, const void* params, const void* X, long 
 jet_status check_call(const jet_plan_s* p, const void* params, const void* X, long long N, const void* source) {
   if (!p) return fail(JET_ERR_INVALID, "NULL plan");
   if (N < 0) return fail(JET_ERR_INVALID, "N < 0");
+  if (p->n_groups > 0) {
+    if ((int)p->group_counts.size() != p->n_groups)
+      return fail(JET_ERR_INVALID, "a composite-loss plan needs jet_plan_set_term_points before its calls");
+    long long tot = 0;
+    for (long long c : p->group_counts) tot += c;
+    if (tot != N) return fail(JET_ERR_INVALID, "N (%lld) differs from the loss terms' points (%lld)", N, tot);
+  }
   if (!params) return fail(JET_ERR_INVALID, "NULL params");
   if (N > 0 && !X) return fail(JET_ERR_INVALID, "NULL X");
   if (p->has_source && N > 0 && !source) return fail(JET_ERR_INVALID, "the residual has a source: pass it");

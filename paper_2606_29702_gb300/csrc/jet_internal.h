@@ -13,12 +13,27 @@ constexpr int kMaxRes = 4;
 constexpr int kMaxOut = 4;
 constexpr int kMaxC = 16;
 
-// One residual monomial: coef * prod fac, fac = o * C + channel index.
+// One residual monomial: coef * prod fac, fac = o * C + channel index; bit f
+// of pmask: factor f is read at the second point of a pair (paired loss terms).
 struct DevTerm {
   double coef;
   int comp;
   int nfac;
   int fac[4];
+  int pmask;
+};
+
+// One term of a composite loss (Sec. 3.1.1: weighted IC, BC and PDE terms over
+// their own blocks of the concatenated points): the points [start, start +
+// count), its monomials [t0, t1), scale = weight / (residuals of the term).
+// A paired term has one residual per consecutive pair of points, evaluated at
+// the pair's first point.
+constexpr int kMaxGroups = 4;
+struct DevGroup {
+  long long start, count;
+  double scale;
+  int t0, t1;
+  int n_res, paired, has_source;
 };
 
 // Kernel modes
@@ -47,6 +62,9 @@ struct DevInstance {
   double inv_N;
   int n_terms;
   DevTerm terms[kMaxTerms];
+  // composite loss (0: one residual over all points, mean over N)
+  int n_groups;
+  DevGroup groups[kMaxGroups];
   // tiling
   int P;               // points per tile
   int pitch;           // smem row pitch (elements) of a jet buffer, >= S * P

@@ -31,6 +31,7 @@
 
 #include "jet_closures_gen.h"
 #include "jet_f2.cuh"
+#include "jet_groups.cuh"
 #include "jet_internal.h"
 
 namespace jet {
@@ -413,6 +414,13 @@ struct SimtTile {
     double loss = 0.0;
     const T* src = reinterpret_cast<const T*>(I.source);
     T* rout = reinterpret_cast<T*>(I.r_out);
+    if (I.n_groups > 0) {  // composite loss: every term over its own points
+      if (bwd)
+        for (int i = threadIdx.x; i < I.n_out * ncol; i += NT) UB[i] = T(0);
+      __syncthreads();
+      return grouped_residual<T>(I.terms, I.groups, I.n_groups, I.n_res, UO, UB, P, n0, nvalid, src, rout, bwd,
+                                 threadIdx.x, NT);
+    }
     const T two_over_n = T(2.0 * I.inv_N);
     const bool parallel = nt <= I.n_out * C && I.n_res * P * (int)sizeof(T) <= 64 * (int)sizeof(double);
     if (!parallel) {

@@ -662,6 +662,7 @@ void fill_tc(const jet_plan_s* p, const TcPlan* t, const void* params, const voi
   I.split3 = t->split3;
   I.n_terms = (int)p->terms.size();
   for (int m = 0; m < I.n_terms; ++m) I.terms[m] = p->terms[m];
+  I.n_groups = p->n_groups > 0 ? jet::fill_groups(p, I.groups) : 0;
   I.params = reinterpret_cast<const float*>(params);
   for (int l = 0; l < p->L; ++l) {
     I.off_W[l] = p->off_W[l];
@@ -672,7 +673,7 @@ void fill_tc(const jet_plan_s* p, const TcPlan* t, const void* params, const voi
   I.source = reinterpret_cast<const float*>(source);
   I.r_out = reinterpret_cast<float*>(r_out);
   I.N = N;
-  I.inv_N = N > 0 ? 1.0 / (double)N : 0.0;
+  I.inv_N = p->n_groups > 0 ? 1.0 : (N > 0 ? 1.0 / (double)N : 0.0);  // a composite loss scales per term
   I.n_tiles = (N + t->P - 1) / t->P;
   long long chunks = std::min<long long>(std::max<long long>(I.n_tiles, 1), t->grid);
   I.tiles_per_chunk = (int)((I.n_tiles + chunks - 1) / chunks);
@@ -1035,6 +1036,8 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
   long long total_tiles = 0;
   for (int i = 0; i < n; ++i) {
     if (N[i] < 1) return tfail(JET_ERR_INVALID, "batched calls need N >= 1 for every instance");
+    if (!jet::group_counts_match(plans[i], N[i]))
+      return tfail(JET_ERR_INVALID, "a composite-loss member's term points do not add up to its N");
     if (!params[i] || !X[i]) return tfail(JET_ERR_INVALID, "NULL params or X in batch");
     if (plans[i]->has_source != (source && source[i])) return tfail(JET_ERR_INVALID, "source does not match spec");
     total_tiles += (N[i] + plans[i]->tcp->P - 1) / plans[i]->tcp->P;

@@ -104,6 +104,8 @@ struct alignas(64) TcInst {
   int wu, G, Pc;
   int n_terms;
   DevTerm terms[kMaxTerms];
+  int n_groups;  // composite loss (0: one residual over all points)
+  DevGroup groups[kMaxGroups];
   const float* params;
   long long off_W[kMaxLayers], off_b[kMaxLayers];
   long long n_params;
@@ -449,6 +451,13 @@ struct TcTile {
     const int P = I.P, nt = I.n_terms, nslot = I.n_out * C;
     const float two_over_n = (float)(2.0 * I.inv_N);
     double loss = 0.0;
+    if (I.n_groups > 0) {  // composite loss: every term over its own points
+      if (bwd)
+        for (int i = tid; i < nslot * P; i += nthr) ub[i] = 0.f;
+      __syncthreads();
+      return grouped_residual<float>(I.terms, I.groups, I.n_groups, I.n_res, uo, ub, P, n0, nvalid, I.source,
+                                     I.r_out, bwd, tid, nthr);
+    }
     if ((nt + I.n_res) * P > nwg * 4 * 256) {
       if (bwd)
         for (int i = tid; i < nslot * P; i += nthr) ub[i] = 0.f;

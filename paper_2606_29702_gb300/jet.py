@@ -42,6 +42,10 @@ class JetResidualSpec(ctypes.Structure):
                 ("mono", ctypes.POINTER(ctypes.POINTER(JetMonomial))), ("has_source", ctypes.c_int32)]
 
 
+class JetLossTerm(ctypes.Structure):
+    _fields_ = [("spec", ctypes.POINTER(JetResidualSpec)), ("weight", ctypes.c_double), ("paired", ctypes.c_int32)]
+
+
 class JetPlanInfo(ctypes.Structure):
     _fields_ = [("d_in", ctypes.c_int32), ("n_out", ctypes.c_int32), ("n_layers", ctypes.c_int32),
                 ("n_channels", ctypes.c_int32), ("closure_class", ctypes.c_int32),
@@ -52,7 +56,7 @@ class JetPlanInfo(ctypes.Structure):
                 ("wgrad_chunk_fp32", ctypes.c_int32)]
 
 
-EXPORTS = ["jet_plan_create", "jet_plan_get_info", "jet_forward_residual", "jet_backward_params", "jet_train_step",
+EXPORTS = ["jet_plan_create", "jet_plan_create_loss", "jet_plan_set_term_points", "jet_plan_get_info", "jet_forward_residual", "jet_backward_params", "jet_train_step",
            "jet_train_step_dev", "jet_plan_destroy", "jet_batch_create", "jet_batch_backward", "jet_batch_train_step",
            "jet_batch_train_step_dev", "jet_batch_destroy",
            "jet_debug_activation", "jet_plan_profile", "jet_plan_profile_read", "jet_backward_params_noalloc",
@@ -72,6 +76,9 @@ def load():
     vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
     L.jet_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(JetResidualSpec), i32, i32,
                                   ctypes.POINTER(i32), i32, ctypes.POINTER(JetChan), i32, sz, i32]
+    L.jet_plan_create_loss.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(JetLossTerm), i32, i32,
+                                       ctypes.POINTER(i32), i32, ctypes.POINTER(JetChan), i32, sz, i32]
+    L.jet_plan_set_term_points.argtypes = [vp, ctypes.POINTER(i64)]
     L.jet_plan_get_info.argtypes = [vp, ctypes.POINTER(JetPlanInfo)]
     L.jet_forward_residual.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp]
     L.jet_backward_params.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp]
@@ -273,6 +280,64 @@ class Plan:
 def _chk_counter(t):
     if not t.is_cuda or t.dtype != torch.int64 or t.numel() != 1:
         raise ValueError("step_counter must be a one-element CUDA int64 tensor")
+
+
+class _LossShape:
+    """What the call checks of a Plan read from its spec, for a composite loss."""
+
+    def __init__(self, terms):
+        specs = [t[0] for t in terms]
+        self.name = "+".join(sp.name for sp in specs)
+        self.d_in = specs[0].d_in
+        self.n_out = specs[0].n_out
+        self.n_res = max(sp.n_res for sp in specs)
+        self.has_source = any(sp.has_source for sp in specs)
+        self._specs = specs
+
+    def closure(self):
+        out = set()
+        for sp in self._specs:
+            out |= set(sp.closure())
+        return sorted(out, key=lambda a: (sum(a), a))
+
+
+class LossPlan(Plan):
+    """A composite-loss plan (jet_plan_create_loss): ``terms`` is a list of
+    (spec, weight, paired) in point order; ``set_term_points`` (or the
+    ``counts`` argument of the calls) gives each term's number of points."""
+
+    def __init__(self, terms, widths, precision="fp32", needed=None, mem_budget=0, store=False, tile=None, ctas=0):
+        L = load()
+        self.tile = tile
+        self.ctas = ctas
+        self.spec = _LossShape(terms)
+        self.widths = list(widths)
+        self.precision = precision
+        structs = [_spec_struct(t[0]) for t in terms]
+        arr = (JetLossTerm * len(terms))()
+        for i, ((sp, w, paired), (s, _)) in enumerate(zip(terms, structs)):
+            arr[i].spec = ctypes.pointer(s)
+            arr[i].weight = float(w)
+            arr[i].paired = 1 if paired else 0
+        needed = self.spec.closure() if needed is None else needed
+        nd = (JetChan * max(1, len(needed)))()
+        for i, al in enumerate(needed):
+            for j, k in enumerate(al):
+                nd[i].alpha[j] = k
+        wd = (ctypes.c_int32 * len(widths))(*widths)
+        flags = FLAG_AUTO_CLOSE | (FLAG_STORE if store else 0) | ((tile // 8) << 8 if tile else 0) | (ctas << 16)
+        h = ctypes.c_void_p()
+        _check(L.jet_plan_create_loss(ctypes.byref(h), len(terms), arr, self.spec.d_in, len(widths) - 1, wd,
+                                      len(needed), nd, PRECISIONS[precision], int(mem_budget), flags))
+        self._h = h
+        self._keep = (structs, arr)
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.counts = None
+
+    def set_term_points(self, counts):
+        c = (ctypes.c_int64 * len(counts))(*[int(x) for x in counts])
+        _check(load().jet_plan_set_term_points(self._h, c))
+        self.counts = list(counts)
 
 
 def _vp_array(ts):

@@ -108,6 +108,32 @@ def ns_uvp(Re=100.0):
     return Spec("ns_uvp", 2, 3, [rc, ru, rv])
 
 
+# jet_chan.out flag of a factor read at the second point of a pair (JET_PAIR_SECOND)
+PAIR_SECOND = 0x100
+
+
+def burgers_loss_terms(nu=0.01, w_ic=1.0, w_bc=1.0, w_pde=1.0):
+    """Composite Burgers loss of Sec. 3.1.1 as (spec, weight, paired) terms, in
+    point order: periodic boundary pairs ((0, t), (1, t)) for u and u_x, the
+    initial condition u(x, 0) - u0(x) (u0 per point as the source) and the
+    PDE residual."""
+    U, X = (0, 0), (1, 0)
+    b = PAIR_SECOND
+    bc = Spec("periodic_bc", 2, 1, [[(1.0, [(0, U)]), (-1.0, [(b, U)])], [(1.0, [(0, X)]), (-1.0, [(b, X)])]])
+    ic = Spec("ic", 2, 1, [[(1.0, [(0, U)])]], has_source=True)
+    return [(bc, w_bc, True), (ic, w_ic, False), (burgers(nu), w_pde, False)]
+
+
+def cavity_loss_terms(Re=100.0, w_wall=1.0, w_lid=1.0, w_pde=1.0):
+    """Composite lid-driven cavity loss of Sec. 3.1.1: the residuals of Eq. 16
+    and the velocity conditions of the no-slip walls and of the lid, u - u_b
+    and v - v_b with (u_b, v_b) per point as the source."""
+    U = (0, 0)
+    vel = [[(1.0, [(0, U)])], [(1.0, [(1, U)])]]
+    return [(ns_uvp(Re), w_pde, False), (Spec("wall", 2, 3, vel, has_source=True), w_wall, False),
+            (Spec("lid", 2, 3, vel, has_source=True), w_lid, False)]
+
+
 FAMILIES = {"burgers": burgers, "ks": ks, "allen_cahn": allen_cahn, "helmholtz": helmholtz, "ns_psi": ns_psi,
             "ns_uvp": ns_uvp}
 # representative coefficients of every family (the build derives each

@@ -23,6 +23,16 @@ involved in the residual loss):
 * ``ns_uvp_2x64x6``: steady Navier-Stokes in primitive variables (u, v, p),
   Re = 100 (Eq. 16), 2->64x6->3 as in Sec. 3.1.1, N = 10000 PDE points
   uniform on the unit square, float32.
+
+and the two composite losses of Sec. 3.1.1 (all points batched), see
+``loss_workload``:
+
+* ``burgers_loss_2x64x6``: Burgers on [0,1]^2, nu = 0.01, 1000 periodic
+  boundary pairs ((0, t), (1, t)), 101 initial-condition points with
+  u0(x) = -sin(2 pi x), 10000 PDE points; 2->64x6->1.
+* ``cavity_loss_2x64x6``: the lid-driven cavity at Re = 100, 10000 PDE points,
+  1499 no-slip wall points (x = 0, x = 1 or y = 0; u = v = 0) and 499 lid
+  points (y = 1; u = 1, v = 0); 2->64x6->3.
 """
 
 import math
@@ -118,3 +128,55 @@ def ensemble(n_burgers=32, n_ac=32, widths=(32, 64, 128), depth=(3, 8), n_range=
         layers = xavier_layers(wid, int(rng.integers(1 << 30)))
         out.append(dict(family=fam, coefs=coefs, widths=wid, N=N, X=X, layers=layers))
     return out
+
+
+LOSS_WORKLOADS = {
+    "burgers_loss_2x64x6": dict(kind="burgers", coefs=dict(nu=0.01), widths=[2] + [64] * 6 + [1],
+                                counts=dict(bc_pairs=1000, ic=101, pde=10000), precision="fp32", seed_pts=0,
+                                seed_par=1),
+    "cavity_loss_2x64x6": dict(kind="cavity", coefs=dict(Re=100.0), widths=[2] + [64] * 6 + [3],
+                               counts=dict(pde=10000, wall=1499, lid=499), precision="fp32", seed_pts=0, seed_par=1),
+}
+
+
+def loss_points(kind, counts, seed):
+    """Concatenated points of a composite loss, in term order, with the
+    per-term point counts and the per-point prescribed values (the source
+    rows: the initial condition, the wall and lid velocities).
+
+    Returns (X [N, 2], term counts, source [N, n_src] or None)."""
+    rng = np.random.default_rng(seed)
+    if kind == "burgers":
+        nb, ni, npde = counts["bc_pairs"], counts["ic"], counts["pde"]
+        t = rng.random(nb)
+        bc = np.empty((2 * nb, 2))
+        bc[0::2, 0], bc[1::2, 0] = 0.0, 1.0
+        bc[0::2, 1] = bc[1::2, 1] = t
+        xi = rng.random(ni)
+        ic = np.column_stack([xi, np.zeros(ni)])
+        pde = rng.random((npde, 2))
+        X = np.concatenate([bc, ic, pde])
+        src = np.zeros((X.shape[0], 2))  # [N][n_res]: the periodic term has two components
+        src[2 * nb:2 * nb + ni, 0] = -np.sin(2.0 * math.pi * xi)
+        return X, [2 * nb, ni, npde], src
+    npde, nw, nl = counts["pde"], counts["wall"], counts["lid"]
+    pde = rng.random((npde, 2))
+    s = rng.random(nw)
+    side = rng.integers(0, 3, nw)
+    wall = np.column_stack([np.where(side == 0, 0.0, np.where(side == 1, 1.0, s)),
+                            np.where(side == 2, 0.0, s)])
+    lid = np.column_stack([rng.random(nl), np.ones(nl)])
+    X = np.concatenate([pde, wall, lid])
+    src = np.zeros((X.shape[0], 3))
+    src[npde + nw:, 0] = 1.0
+    return X, [npde, nw, nl], src
+
+
+def loss_workload(name, scale=1.0):
+    """(spec dict, X, term counts, source, layers) of a composite-loss
+    workload; ``scale`` multiplies every point count (pairs stay pairs)."""
+    spec = dict(LOSS_WORKLOADS[name])
+    counts = {k: max(1, int(round(v * scale))) for k, v in spec["counts"].items()}
+    X, cnt, src = loss_points(spec["kind"], counts, spec["seed_pts"])
+    layers = xavier_layers(spec["widths"], spec["seed_par"])
+    return spec, X, cnt, src, layers
