@@ -112,6 +112,21 @@ for _fam, _coefs in _SPECS.FAMILY_DEFAULTS.items():
 for _i, (_d, _chans) in enumerate(_parse_extra(os.environ.get("JET_EXTRA_CLASSES", ""))):
     _add("extra%d" % _i, _d, _chans)
 
+# Tensor-core tile shapes compiled with compile-time constants (points per
+# sub-tile, packed sub-tiles, 128-row halves, MMA width, CTA threads) besides
+# the general kernel: the plans' built-in tile choices for the benchmarked
+# networks of each class.  Other shapes and batches run the general kernel.
+# A G of 0 leaves the packing to the work item: batches of members with widths
+# 32, 64 and 128 and the same points per sub-tile (the ensemble) use it.  The
+# launch takes the first entry that matches, so exact shapes come first.
+FAST_SHAPES = {
+    "burgers": [(64, 2, 1, 128, 512), (64, 0, 1, 128, 512)],  # width-64 nets (P = 128); ensembles, Pc = 64
+    "ks": [(40, 2, 1, 128, 512), (32, 2, 1, 128, 512)],        # 2->64x5->1: BF16 P = 80, BF16X3 P = 64
+    "helmholtz": [(16, 1, 2, 256, 512), (8, 1, 2, 256, 512)],  # 3->256x8->1: store P = 16, per tile P = 8
+    "ns_psi": [(16, 1, 1, 128, 512), (8, 1, 1, 128, 512)],     # 3->128x6->2: BF16 P = 16, BF16X3 P = 8
+    "ns_uvp": [(48, 2, 1, 128, 512)],                          # 2->64x6->3: P = 96
+}
+
 
 def set_partitions(items):
     if not items:
@@ -277,6 +292,11 @@ def emit(path):
     out.append("template <int ID> struct ClassById;")
     for i, n in enumerate(CLASSES):
         out.append("template <> struct ClassById<%d> { using type = Cls_%s; };" % (i, n))
+    out.append("")
+    out.append("// per class id: JET_TC_SHAPES_<id>(M) expands M(PC, G, H, W, NT) for every compiled fixed shape")
+    for i, n in enumerate(CLASSES):
+        shapes = FAST_SHAPES.get(n, [])
+        out.append("#define JET_TC_SHAPES_%d(M) %s" % (i, " ".join("M(%d, %d, %d, %d, %d)" % t for t in shapes)))
     out.append("")
     out.append("// X-macro over the classes: JET_FOR_EACH_CLASS(M) expands M(id, Cls_name)")
     out.append("#define JET_FOR_EACH_CLASS(M) \\")

@@ -770,6 +770,10 @@ jet_status run(jet_plan_s* p, TcPlan* t, int mode, const TcInst& I, cudaStream_t
   TcArgs a;
   memset(&a, 0, sizeof(a));
   a.inst0 = I;
+  a.shape[0] = I.Pc;
+  a.shape[1] = I.G;
+  a.shape[2] = I.H;
+  a.shape[3] = I.w;
   a.mode = mode;
   a.n_items = I.n_chunks;
   a.insts = nullptr;
@@ -1117,6 +1121,12 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
   }
   TcArgs a;
   memset(&a, 0, sizeof(a));
+  for (int k = 0; k < 4; ++k) {  // the members' common tile shape (0 where they differ)
+    auto field = [&](const TcInst& I) { return k == 0 ? I.Pc : k == 1 ? I.G : k == 2 ? I.H : I.w; };
+    a.shape[k] = field(insts[0]);
+    for (int i = 1; i < n; ++i)
+      if (field(insts[i]) != a.shape[k]) a.shape[k] = 0;
+  }
   a.mode = MODE_FWD_BWD;
   a.n_items = base;
   a.insts = b->d_insts;

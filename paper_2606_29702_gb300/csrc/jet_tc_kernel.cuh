@@ -139,6 +139,10 @@ struct alignas(64) TcInst {
 
 struct TcArgs {
   TcInst inst0;
+  // tile shape shared by every work item of the launch (points per sub-tile,
+  // packed sub-tiles, 128-row halves, MMA width), 0 where they differ: selects
+  // a fixed-shape kernel when one is compiled
+  int shape[4];
   int mode;
   int n_items;
   const TcInst* insts;
@@ -148,13 +152,37 @@ struct TcArgs {
   int nthreads;  // launch block size: 256 or 512
 };
 
-template <class Cls>
+// Tile shape of a launch: points per sub-tile PC, packed sub-tiles G, 128-row
+// halves H, MMA width W and CTA threads NT as compile-time constants, or 0 for
+// the runtime values of the work item's descriptor and launch (a batch of
+// members with different packings fixes PC, H, W and NT and leaves G).  Fixed shapes let the compiler fold
+// the TMEM column and swizzled shared-memory offsets of every epilogue access.
+template <int PC_, int G_, int H_, int W_, int NT_>
+struct TcShape {
+  static constexpr int PC = PC_, G = G_, H = H_, W = W_, NT = NT_;
+};
+using TcShapeAny = TcShape<0, 0, 0, 0, 0>;
+
+template <class Cls, class Shape = TcShapeAny>
 struct TcTile {
   static constexpr int C = Cls::C;
   static constexpr int NP = Cls::NP;
   static constexpr int TOP = Cls::TOP_BEGIN;
   static constexpr int PPF = C >= 7 ? 2 : 4;   // points per epilogue pass (forward)
   static constexpr int PPB = C >= 5 ? 2 : 4;   // points per epilogue pass (adjoint)
+
+  // the tile shape: compile-time when the launch fixes it, else the descriptor's
+  __device__ __forceinline__ int pc() const { return Shape::PC ? Shape::PC : I.Pc; }
+  __device__ __forceinline__ int gg() const { return Shape::G ? Shape::G : I.G; }
+  __device__ __forceinline__ int hh() const { return Shape::H ? Shape::H : I.H; }
+  __device__ __forceinline__ int ww() const { return Shape::W ? Shape::W : I.w; }
+  __device__ __forceinline__ int wuu() const { return Shape::W && Shape::G ? Shape::W / Shape::G : I.wu; }
+  __device__ __forceinline__ int pp() const { return pc() * gg(); }
+  __device__ __forceinline__ int rr() const { return Shape::H ? 128 * Shape::H : R_; }  // rows of every operand buffer
+  __device__ __forceinline__ int cpad() const { return Shape::PC ? (C * Shape::PC + 15) / 16 * 16 : I.cols_pad; }
+  __device__ __forceinline__ int ctop() const { return Shape::PC ? (C - TOP) * Shape::PC : I.top_cols; }
+  __device__ __forceinline__ int nth() const { return Shape::NT ? Shape::NT : nthr; }   // threads of the CTA
+  __device__ __forceinline__ int nw() const { return Shape::NT ? Shape::NT / 128 : nwg; }  // warpgroups
 
   const TcInst& I;      // the work item's descriptor, copied to shared memory
   const TcInst* Imap;   // the same descriptor in param or global space: its tensor maps serve TMA
@@ -167,7 +195,7 @@ struct TcTile {
   uint32_t tmem;
   uint32_t ph_tma, ph_mma, ph_ld;
   int tid, warp;
-  int R;        // rows of every operand buffer (128 * H)
+  int R_;       // rows of every operand buffer (128 * H), for a runtime shape
   float* part;  // per-warpgroup partial sums [nwg][4][256]
   int q, wg, ul;  // TMEM lane quadrant, warpgroup, unit within a 128-row half
   int nwg, nthr;  // warpgroups and threads of the CTA
@@ -181,7 +209,7 @@ struct TcTile {
   __device__ unsigned char* ACT(int i) const { return sm + (i ? I.o_a1 : I.o_a0); }
   __device__ unsigned char* ALO(int i) const { return sm + (i ? I.o_alo1 : I.o_alo0); }
   __device__ uint32_t R0(int h) const { return tmem + (uint32_t)(h * I.r0w); }
-  __device__ uint32_t R1(int h) const { return tmem + (uint32_t)(I.H * I.r0w + h * I.r1w); }
+  __device__ uint32_t R1(int h) const { return tmem + (uint32_t)(hh() * I.r0w + h * I.r1w); }
   __device__ uint32_t lane_base() const { return (uint32_t)(q * 32) << 16; }
   __device__ float& PART(int w, int k, int u) const { return part[(w * 4 + k) * 256 + u]; }
 
@@ -199,8 +227,8 @@ struct TcTile {
 
   // ------------------------------------------------------------ loads (thread 0)
   __device__ void load_hidden_w(int l) {  // W^l, l = 2..L-1 -> W buffer (and W_lo)
-    const int nck = I.w / 64 > 2 ? I.w / 64 : 2;
-    const uint32_t box = 64u * R * 2u;
+    const int nck = ww() / 64 > 2 ? ww() / 64 : 2;
+    const uint32_t box = 64u * rr() * 2u;
     tc::mbar_arrive_expect_tx(bar_tma, box * nck * (I.split3 ? 2u : 1u));
     for (int kc = 0; kc < nck; ++kc) {
       tc::tma_load_3d(sm + I.o_w + kc * box, &Imap->wmap, bar_tma, kc * 64, 0, l - 2);
@@ -209,7 +237,7 @@ struct TcTile {
   }
 
   __device__ void load_out_w() {  // W^L -> W buffer, 128-row boxes
-    const int nck = (I.w + 63) / 64;
+    const int nck = (ww() + 63) / 64;
     const uint32_t box = 64u * 128u * 2u;
     tc::mbar_arrive_expect_tx(bar_tma, box * nck);
     for (int kc = 0; kc < nck; ++kc) tc::tma_load_2d(sm + I.o_w + kc * box, &Imap->wlmap, bar_tma, kc * 64, 0);
@@ -246,11 +274,11 @@ struct TcTile {
   __device__ void mma_layer(int bi) {
     const uint32_t sW = tc::smem_u32(sm + I.o_w), sWlo = tc::smem_u32(sm + I.o_wlo);
     const uint32_t sB = tc::smem_u32(ACT(bi)), sBlo = tc::smem_u32(ALO(bi));
-    const uint32_t chunkW = (uint32_t)(R / 8) * 1024u, chunkA = chunkW;
-    const uint32_t id = tc::idesc_bf16(128, I.cols_pad, 0, 1);
-    const uint32_t id_top = tc::idesc_bf16(128, I.top_cols, 0, 1);
-    const int ks = I.w / 16;
-    for (int h = 0; h < I.H; ++h) {
+    const uint32_t chunkW = (uint32_t)(rr() / 8) * 1024u, chunkA = chunkW;
+    const uint32_t id = tc::idesc_bf16(128, cpad(), 0, 1);
+    const uint32_t id_top = tc::idesc_bf16(128, ctop(), 0, 1);
+    const int ks = ww() / 16;
+    for (int h = 0; h < hh(); ++h) {
       for (int s = 0; s < ks; ++s) {
         const uint32_t aoff = (uint32_t)(s / 4) * chunkW + (uint32_t)h * 16384u + (uint32_t)(s % 4) * 32u;
         const uint64_t ad = tc::sdesc(sW + aoff, 16, 1024);
@@ -271,9 +299,9 @@ struct TcTile {
 
   __device__ void mma_out(int bi) {  // D[R1(0)] = W^L (rows >= n_out zero) x A^{L-1}
     const uint32_t sW = tc::smem_u32(sm + I.o_w), sB = tc::smem_u32(ACT(bi));
-    const uint32_t chunkA = (uint32_t)(R / 8) * 1024u;
-    const uint32_t id = tc::idesc_bf16(128, I.cols_pad, 0, 1);
-    for (int s = 0; s < I.w / 16; ++s) {
+    const uint32_t chunkA = (uint32_t)(rr() / 8) * 1024u;
+    const uint32_t id = tc::idesc_bf16(128, cpad(), 0, 1);
+    for (int s = 0; s < ww() / 16; ++s) {
       const uint64_t ad = tc::sdesc(sW + (uint32_t)(s / 4) * 16384u + (uint32_t)(s % 4) * 32u, 16, 1024);
       const uint64_t bd = tc::sdesc(sB + (uint32_t)s * 2048u, chunkA, 1024);
       tc::mma_f16(R1(0), ad, bd, id, s > 0);
@@ -283,10 +311,10 @@ struct TcTile {
   // D[R1] = W^l^T (MN-major A) x Zbar (MN-major B)
   __device__ void mma_dgrad(int zi) {
     const uint32_t sW = tc::smem_u32(sm + I.o_w), sZ = tc::smem_u32(ACT(zi));
-    const uint32_t chunk = (uint32_t)(R / 8) * 1024u;
-    const uint32_t id = tc::idesc_bf16(128, I.cols_pad, 1, 1);
-    for (int h = 0; h < I.H; ++h)
-      for (int s = 0; s < I.w / 16; ++s) {
+    const uint32_t chunk = (uint32_t)(rr() / 8) * 1024u;
+    const uint32_t id = tc::idesc_bf16(128, cpad(), 1, 1);
+    for (int h = 0; h < hh(); ++h)
+      for (int s = 0; s < ww() / 16; ++s) {
         const uint64_t ad = tc::sdesc(sW + (uint32_t)(2 * h) * chunk + (uint32_t)s * 2048u, chunk, 1024);
         const uint64_t bd = tc::sdesc(sZ + (uint32_t)s * 2048u, chunk, 1024);
         tc::mma_f16(R1(h), ad, bd, id, s > 0);
@@ -296,10 +324,10 @@ struct TcTile {
   // D[R0] = Zbar (K-major, M = out units) x A^{l-1} (K-major, N block nb of in units)
   __device__ void mma_wgrad(int zi, int ai, int nb, int NB) {
     const uint32_t sZ = tc::smem_u32(ACT(zi)), sA = tc::smem_u32(ACT(ai));
-    const uint32_t chunk = (uint32_t)(R / 8) * 1024u;
+    const uint32_t chunk = (uint32_t)(rr() / 8) * 1024u;
     const uint32_t id = tc::idesc_bf16(128, NB, 0, 0);
-    for (int h = 0; h < I.H; ++h)
-      for (int s = 0; s < I.cols_pad / 16; ++s) {
+    for (int h = 0; h < hh(); ++h)
+      for (int s = 0; s < cpad() / 16; ++s) {
         const uint32_t koff = (uint32_t)(s / 4) * chunk + (uint32_t)(s % 4) * 32u;
         const uint64_t ad = tc::sdesc(sZ + koff + (uint32_t)h * 16384u, 16, 1024);
         const uint64_t bd = tc::sdesc(sA + koff + (uint32_t)(nb * NB / 8) * 1024u, 16, 1024);
@@ -310,7 +338,7 @@ struct TcTile {
   // ------------------------------------------------------------ epilogue helpers
   template <int PP>
   __device__ void st_bf16(unsigned char* buf, int row, int col, const float* v) const {
-    unsigned char* p = buf + tc::swz_off(row, col & ~7, R) + (col & 7) * 2;
+    unsigned char* p = buf + tc::swz_off(row, col & ~7, rr()) + (col & 7) * 2;
     if (PP == 4) {
       __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
       __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
@@ -335,18 +363,18 @@ struct TcTile {
   // ------------------------------------------------------------ forward pieces
   __device__ void layer1_fwd(int out_buf) {
     const float* Pm = I.params;
-    const int Pc = I.Pc;
+    const int Pc = pc();
     constexpr int d = Cls::D;  // the plan's input dimension
-    for (int h = 0; h < I.H; ++h) {
+    for (int h = 0; h < hh(); ++h) {
       const int r = h * 128 + ul;  // operand row
-      if (r >= I.w) continue;
-      const int sub = r / I.wu, u = r - sub * I.wu;
+      if (r >= ww()) continue;
+      const int sub = r / wuu(), u = r - sub * wuu();
       float w1[d];
 #pragma unroll
       for (int i = 0; i < d; ++i) w1[i] = Pm[I.off_W[0] + u * d + i];
       const float b1 = Pm[I.off_b[0] + u];
       const float* xs = XS() + sub * Pc * d;
-      for (int g = wg * PPF; g < Pc; g += nwg * PPF) {
+      for (int g = wg * PPF; g < Pc; g += nw() * PPF) {
         float av[C][PPF];
 #pragma unroll
         for (int j = 0; j < PPF; j += 2) {
@@ -384,12 +412,12 @@ struct TcTile {
 
   // a^l = compose(D[R0] + b^l) -> ACT(out_buf)
   __device__ void hidden_epilogue(int l, int out_buf) {
-    const int Pc = I.Pc;
-    for (int h = 0; h < I.H; ++h) {
+    const int Pc = pc();
+    for (int h = 0; h < hh(); ++h) {
       const int r = h * 128 + ul;
-      if (h * 128 + q * 32 >= I.w) continue;  // warp-uniform
-      const float bu = I.params[I.off_b[l - 1] + r % I.wu];
-      for (int g = wg * PPF; g < Pc; g += nwg * PPF) {
+      if (h * 128 + q * 32 >= ww()) continue;  // warp-uniform
+      const float bu = I.params[I.off_b[l - 1] + r % wuu()];
+      for (int g = wg * PPF; g < Pc; g += nw() * PPF) {
         float zv[C][PPF];
 #pragma unroll
         for (int c = 0; c < C; ++c) tc::tmem_ld<PPF>(R0(h) + lane_base() + (uint32_t)(blk(c) * Pc + g), zv[c]);
@@ -424,8 +452,8 @@ struct TcTile {
   // own quadrant, and all warps split the column groups.
   __device__ void out_epilogue() {
     float* uo = UO();
-    const int Pc = I.Pc, ng = Pc / 8, nrow = I.G * I.n_out, lane = tid & 31;
-    for (int k = wg * 4 + q; k < C * ng; k += nwg * 4) {
+    const int Pc = pc(), ng = Pc / 8, nrow = gg() * I.n_out, lane = tid & 31;
+    for (int k = wg * 4 + q; k < C * ng; k += nw() * 4) {
       const int c = k / ng, g = (k - c * ng) * 8;
       float v[8];
       tc::tmem_ld8(R1(0) + lane_base() + (uint32_t)(blk(c) * Pc + g), v);
@@ -434,7 +462,7 @@ struct TcTile {
         const int sub = lane / I.n_out, o = lane - sub * I.n_out;
         const float b = c == 0 ? I.params[I.off_b[I.L - 1] + o] : 0.f;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) uo[(o * C + c) * I.P + sub * Pc + g + j] = v[j] + b;
+        for (int j = 0; j < 8; ++j) uo[(o * C + c) * pp() + sub * Pc + g + j] = v[j] + b;
       }
     }
   }
@@ -448,21 +476,21 @@ struct TcTile {
   __device__ double residual(long long n0, int nvalid, bool bwd) {
     float* uo = UO();
     float* ub = UB();
-    const int P = I.P, nt = I.n_terms, nslot = I.n_out * C;
+    const int P = pp(), nt = I.n_terms, nslot = I.n_out * C;
     const float two_over_n = (float)(2.0 * I.inv_N);
     double loss = 0.0;
     if (I.n_groups > 0) {  // composite loss: every term over its own points
       if (bwd)
-        for (int i = tid; i < nslot * P; i += nthr) ub[i] = 0.f;
+        for (int i = tid; i < nslot * P; i += nth()) ub[i] = 0.f;
       __syncthreads();
       return grouped_residual<float>(I.terms, I.groups, I.n_groups, I.n_res, uo, ub, P, n0, nvalid, I.source,
-                                     I.r_out, bwd, tid, nthr);
+                                     I.r_out, bwd, tid, nth());
     }
-    if ((nt + I.n_res) * P > nwg * 4 * 256) {
+    if ((nt + I.n_res) * P > nw() * 4 * 256) {
       if (bwd)
-        for (int i = tid; i < nslot * P; i += nthr) ub[i] = 0.f;
+        for (int i = tid; i < nslot * P; i += nth()) ub[i] = 0.f;
       __syncthreads();
-      for (int n = tid; n < nvalid; n += nthr) {
+      for (int n = tid; n < nvalid; n += nth()) {
         float r[kMaxRes];
         for (int c = 0; c < I.n_res; ++c) r[c] = I.source ? -I.source[(n0 + n) * I.n_res + c] : 0.f;
         for (int m = 0; m < nt; ++m) {
@@ -491,7 +519,7 @@ struct TcTile {
     }
     float* prodm = part;            // [n_terms][P] monomial values
     float* rg = part + nt * P;      // [n_res][P] 2 r / N
-    for (int i = tid; i < nt * nvalid; i += nthr) {
+    for (int i = tid; i < nt * nvalid; i += nth()) {
       const int m = i / nvalid, n = i - m * nvalid;
       const DevTerm& tm = I.terms[m];
       float prod = (float)tm.coef;
@@ -499,7 +527,7 @@ struct TcTile {
       prodm[m * P + n] = prod;
     }
     __syncthreads();
-    for (int n = tid; n < nvalid; n += nthr) {
+    for (int n = tid; n < nvalid; n += nth()) {
       const int nres = I.n_res;
       float r[kMaxRes];
 #pragma unroll
@@ -521,7 +549,7 @@ struct TcTile {
     }
     if (!bwd) return loss;
     __syncthreads();
-    for (int i = tid; i < nslot * P; i += nthr) {
+    for (int i = tid; i < nslot * P; i += nth()) {
       const int k = i / P, n = i - k * P;
       float acc = 0.f;
       if (n < nvalid)
@@ -547,17 +575,17 @@ struct TcTile {
   // out_grads_flush after a barrier)
   __device__ void out_grads(int a_buf) {
     const float* ub = UB();
-    const int P = I.P, Pc = I.Pc;
-    for (int h = 0; h < I.H; ++h) {
+    const int P = pp(), Pc = pc();
+    for (int h = 0; h < hh(); ++h) {
       const int r = h * 128 + ul;
-      if (r >= I.w) continue;
-      const int sub = r / I.wu;
+      if (r >= ww()) continue;
+      const int sub = r / wuu();
       const int nout = I.n_out;
       float acc[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
-      for (int c = wg; c < C; c += nwg)
+      for (int c = wg; c < C; c += nw())
         for (int q8 = 0; q8 < Pc; q8 += 8) {
           const int col = blk(c) * Pc + q8;
-          const uint4 raw = *reinterpret_cast<const uint4*>(ACT(a_buf) + tc::swz_off(r, col, R));
+          const uint4 raw = *reinterpret_cast<const uint4*>(ACT(a_buf) + tc::swz_off(r, col, rr()));
           const __nv_bfloat16* bv = reinterpret_cast<const __nv_bfloat16*>(&raw);
           const float* ubc = ub + c * P + sub * Pc + q8;
 #pragma unroll
@@ -578,19 +606,19 @@ struct TcTile {
   // adds across tiles follow)
   __device__ double part_sum(int k, int u) const {
     float s = 0.f;
-    for (int sub = 0; sub < I.G; ++sub)
-      for (int w2 = 0; w2 < nwg; ++w2) s += PART(w2, k, sub * I.wu + u);
+    for (int sub = 0; sub < gg(); ++sub)
+      for (int w2 = 0; w2 < nw(); ++w2) s += PART(w2, k, sub * wuu() + u);
     return (double)s;
   }
 
   __device__ void out_grads_flush(double* g) {
     const float* ub = UB();
-    const int P = I.P, L = I.L;
+    const int P = pp(), L = I.L;
     if (wg == 0)
-      for (int h = 0; h < I.H; ++h) {
+      for (int h = 0; h < hh(); ++h) {
         const int k = h * 128 + ul;
-        if (k >= I.wu) continue;
-        for (int o = 0; o < I.n_out; ++o) tc::red_add_f64(g + I.off_W[L - 1] + (long long)o * I.wu + k, part_sum(o, k));
+        if (k >= wuu()) continue;
+        for (int o = 0; o < I.n_out; ++o) tc::red_add_f64(g + I.off_W[L - 1] + (long long)o * wuu() + k, part_sum(o, k));
       }
     if (tid < I.n_out) {
       float s = 0.f;
@@ -602,9 +630,9 @@ struct TcTile {
   // slot k of PART summed over warpgroups and sub-tiles -> FP64 slice at dst[u * stride]
   __device__ void part_flush(int k, double* dst, int stride) {
     if (wg != 0) return;
-    for (int h = 0; h < I.H; ++h) {
+    for (int h = 0; h < hh(); ++h) {
       const int u = h * 128 + ul;
-      if (u >= I.wu) continue;
+      if (u >= wuu()) continue;
       tc::red_add_f64(dst + (long long)u * stride, part_sum(k, u));
     }
   }
@@ -612,21 +640,21 @@ struct TcTile {
   // Zbar^l = (d compose/dz)^T Abar^l -> ACT(z_buf); db^l += sum_n Zbar_0
   __device__ void adjoint_epilogue(int l, int z_buf, bool abar_from_ub) {
     const float* ub = UB();
-    const int P = I.P, Pc = I.Pc;
-    for (int h = 0; h < I.H; ++h) {
+    const int P = pp(), Pc = pc();
+    for (int h = 0; h < hh(); ++h) {
       const int r = h * 128 + ul;
-      if (h * 128 + q * 32 >= I.w) continue;
-      const int sub = r / I.wu, u = r - sub * I.wu;
+      if (h * 128 + q * 32 >= ww()) continue;
+      const int sub = r / wuu(), u = r - sub * wuu();
       const float bu = I.params[I.off_b[l - 1] + u];
       const int nout = I.n_out;
       float wl[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
       if (abar_from_ub) {
 #pragma unroll
         for (int o = 0; o < kMaxOut; ++o)
-          if (o < nout) wl[o] = I.params[I.off_W[I.L - 1] + (long long)o * I.wu + u];
+          if (o < nout) wl[o] = I.params[I.off_W[I.L - 1] + (long long)o * wuu() + u];
       }
       float gb = 0.f;
-      for (int g = wg * PPB; g < Pc; g += nwg * PPB) {
+      for (int g = wg * PPB; g < Pc; g += nw() * PPB) {
         float zv[C][PPB], abv[C][PPB];
 #pragma unroll
         for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R0(h) + lane_base() + (uint32_t)(blk(c) * Pc + g), zv[c]);
@@ -683,12 +711,12 @@ struct TcTile {
   // tiles in program order, so the sums are deterministic.
   __device__ float* wacc(int l) const {
     return reinterpret_cast<float*>(I.scratch + (long long)blockIdx.x * I.scratch_stride + I.wacc_off) +
-           (long long)(l - 2) * I.G * I.wu * I.wu;
+           (long long)(l - 2) * gg() * wuu() * wuu();
   }
   __device__ void wacc_zero() {
     float4* a = reinterpret_cast<float4*>(wacc(2));
-    const long long n4 = (long long)(I.L - 2) * I.G * I.wu * I.wu / 4;
-    for (long long i = tid; i < n4; i += nthr) a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const long long n4 = (long long)(I.L - 2) * gg() * wuu() * wuu() / 4;
+    for (long long i = tid; i < n4; i += nth()) a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 
   // TMEM columns of lane row (8, from taddr) -> accumulator columns k0 .. k0+7
@@ -697,7 +725,7 @@ struct TcTile {
     float v[8];
     tc::tmem_ld8(taddr, v);
     tc::tmem_wait_ld();
-    const int wu = I.wu;
+    const int wu = wuu();
     tc::red_add_v4_hint(acc + ((long long)(k0 / 4) * wu + u) * 4, v[0], v[1], v[2], v[3], pol);
     tc::red_add_v4_hint(acc + ((long long)(k0 / 4 + 1) * wu + u) * 4, v[4], v[5], v[6], v[7], pol);
   }
@@ -708,18 +736,18 @@ struct TcTile {
   // belong to different points.
   __device__ void acc_wgrad(int l, int nb, int NB) {
     float* acc = wacc(l);
-    const int wu = I.wu;
+    const int wu = wuu();
     const uint64_t pol = tc::policy_evict_last();
-    if (I.G > 1) {  // packed plans have H == 1
+    if (gg() > 1) {  // packed plans have H == 1
       const int sub = ul / wu, j = ul - sub * wu;
       float* a = acc + (long long)sub * wu * wu;
-      for (int k0 = wg * 8; k0 < wu; k0 += nwg * 8)
+      for (int k0 = wg * 8; k0 < wu; k0 += nw() * 8)
         acc8(a, j, k0, R0(0) + lane_base() + (uint32_t)(sub * wu + k0), pol);
       return;
     }
-    for (int h = 0; h < I.H; ++h) {
-      if (h * 128 + q * 32 >= I.w) continue;  // warp-uniform
-      for (int k0 = wg * 8; k0 < NB; k0 += nwg * 8)
+    for (int h = 0; h < hh(); ++h) {
+      if (h * 128 + q * 32 >= ww()) continue;  // warp-uniform
+      for (int k0 = wg * 8; k0 < NB; k0 += nw() * 8)
         acc8(acc, h * 128 + ul, nb * NB + k0, R0(h) + lane_base() + (uint32_t)k0, pol);
     }
   }
@@ -728,25 +756,25 @@ struct TcTile {
   // consecutive threads take consecutive weights, eight per batch with their
   // loads in flight before the adds
   __device__ void chunk_flush(double* g) {
-    const int wu = I.wu, per = wu * wu;
+    const int wu = wuu(), per = wu * wu;
     for (int l = 2; l <= I.L - 1; ++l) {
       const float* acc = wacc(l);
       double* gW = g + I.off_W[l - 1];
-      for (int e0 = tid; e0 < per; e0 += 8 * nthr) {
+      for (int e0 = tid; e0 < per; e0 += 8 * nth()) {
         float v[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const int e = e0 + j * nthr;
+          const int e = e0 + j * nth();
           v[j] = 0.f;
           if (e < per) {
             const int u = e / wu, k = e - u * wu;
-            for (int sub = 0; sub < I.G; ++sub)
+            for (int sub = 0; sub < gg(); ++sub)
               v[j] += __ldcg(acc + ((long long)(sub * (wu / 4) + k / 4) * wu + u) * 4 + (k & 3));
           }
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          if (e0 + j * nthr < per) tc::red_add_f64(gW + e0 + j * nthr, (double)v[j]);
+          if (e0 + j * nth() < per) tc::red_add_f64(gW + e0 + j * nth(), (double)v[j]);
       }
     }
   }
@@ -755,12 +783,12 @@ struct TcTile {
   __device__ void layer1_bwd(bool abar_from_ub) {
     const float* Pm = I.params;
     const float* ub = UB();
-    const int P = I.P, Pc = I.Pc;
+    const int P = pp(), Pc = pc();
     constexpr int d = Cls::D;  // the plan's input dimension
-    for (int h = 0; h < I.H; ++h) {
+    for (int h = 0; h < hh(); ++h) {
       const int r = h * 128 + ul;
-      if (h * 128 + q * 32 >= I.w) continue;
-      const int sub = r / I.wu, u = r - sub * I.wu;
+      if (h * 128 + q * 32 >= ww()) continue;
+      const int sub = r / wuu(), u = r - sub * wuu();
       float w1[d];
 #pragma unroll
       for (int i = 0; i < d; ++i) w1[i] = Pm[I.off_W[0] + u * d + i];
@@ -770,13 +798,13 @@ struct TcTile {
       if (abar_from_ub) {
 #pragma unroll
         for (int o = 0; o < kMaxOut; ++o)
-          if (o < nout) wl[o] = Pm[I.off_W[I.L - 1] + (long long)o * I.wu + u];
+          if (o < nout) wl[o] = Pm[I.off_W[I.L - 1] + (long long)o * wuu() + u];
       }
       const float* xs = XS() + sub * Pc * d;
       float gw[d], gb = 0.f;
 #pragma unroll
       for (int i = 0; i < d; ++i) gw[i] = 0.f;
-      for (int g = wg * PPB; g < Pc; g += nwg * PPB) {
+      for (int g = wg * PPB; g < Pc; g += nw() * PPB) {
         float abv[C][PPB];
         if (!abar_from_ub) {
 #pragma unroll
@@ -846,7 +874,7 @@ struct TcTile {
 
   // ------------------------------------------------------------ one tile
   __device__ double tile(long long t, int mode, double* g) {
-    const int P = I.P, L = I.L, d = I.d;
+    const int P = pp(), L = I.L, d = I.d;
     const bool bwd = mode != MODE_FWD;
     const long long n0 = t * P;
     const long long rem = I.N - n0;
@@ -855,7 +883,7 @@ struct TcTile {
     const bool store = bwd && I.wstore != nullptr;
     const int last_a = store ? L - 2 : L - 3;  // highest A^l copied out of shared memory
     float* xs = XS();
-    for (int i = tid; i < P * d; i += nthr) {
+    for (int i = tid; i < P * d; i += nth()) {
       const int n = i / d;
       xs[i] = n < nvalid ? I.X[(n0 + n) * d + (i % d)] : 0.f;
     }
@@ -970,8 +998,8 @@ struct TcTile {
         sync();
         continue;
       }
-      const int NB = I.H == 2 ? 128 : I.w;
-      const int nblk = I.w / NB;
+      const int NB = hh() == 2 ? 128 : ww();
+      const int nblk = ww() / NB;
       if (tid == 0) {
         mma_dgrad(zb);
         mma_wgrad(zb, ain, 0, NB);
@@ -1003,7 +1031,7 @@ struct TcTile {
   }
 };
 
-template <class Cls>
+template <class Cls, class Shape>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant__ TcArgs args) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t bars[3];
@@ -1066,7 +1094,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
       __syncthreads();
       prev_inst = ii;
     }
-    TcTile<Cls> T{I,
+    TcTile<Cls, Shape> T{I,
                   &Ig,
                   sm,
                   &bars[0],
