@@ -199,6 +199,13 @@ struct TcTile {
   float* part;  // per-warpgroup partial sums [nwg][4][256]
   int q, wg, ul;  // TMEM lane quadrant, warpgroup, unit within a 128-row half
   int nwg, nthr;  // warpgroups and threads of the CTA
+  // descriptor fields of the epilogues' hot accesses, read once per tile: the
+  // shared addresses of the operand buffers and the TMEM region widths
+  uint32_t act_s0 = tc::smem_u32(sm + I.o_a0), act_s1 = tc::smem_u32(sm + I.o_a1);
+  uint32_t alo_s0 = tc::smem_u32(sm + I.o_alo0), alo_s1 = tc::smem_u32(sm + I.o_alo1);
+  uint32_t r0w_ = (uint32_t)I.r0w, r1w_ = (uint32_t)I.r1w;
+  __device__ __forceinline__ uint32_t act_s(int i) const { return i ? act_s1 : act_s0; }
+  __device__ __forceinline__ uint32_t alo_s(int i) const { return i ? alo_s1 : alo_s0; }
 
   // column block of channel c: highest-order channels first
   static __device__ __forceinline__ int blk(int c) { return c >= TOP ? c - TOP : c + (C - TOP); }
@@ -208,8 +215,8 @@ struct TcTile {
   __device__ float* XS() const { return reinterpret_cast<float*>(sm + I.o_xs); }
   __device__ unsigned char* ACT(int i) const { return sm + (i ? I.o_a1 : I.o_a0); }
   __device__ unsigned char* ALO(int i) const { return sm + (i ? I.o_alo1 : I.o_alo0); }
-  __device__ uint32_t R0(int h) const { return tmem + (uint32_t)(h * I.r0w); }
-  __device__ uint32_t R1(int h) const { return tmem + (uint32_t)(hh() * I.r0w + h * I.r1w); }
+  __device__ uint32_t R0(int h) const { return tmem + (uint32_t)h * r0w_; }
+  __device__ uint32_t R1(int h) const { return tmem + (uint32_t)hh() * r0w_ + (uint32_t)h * r1w_; }
   __device__ uint32_t lane_base() const { return (uint32_t)(q * 32) << 16; }
   __device__ float& PART(int w, int k, int u) const { return part[(w * 4 + k) * 256 + u]; }
 
@@ -336,24 +343,22 @@ struct TcTile {
   }
 
   // ------------------------------------------------------------ epilogue helpers
+  // PP values of one operand row (consecutive columns) as BF16; buf is the
+  // buffer's shared address
   template <int PP>
-  __device__ void st_bf16(unsigned char* buf, int row, int col, const float* v) const {
-    unsigned char* p = buf + tc::swz_off(row, col & ~7, rr()) + (col & 7) * 2;
+  __device__ void st_bf16(uint32_t buf, int row, int col, const float* v) const {
+    const uint32_t p = buf + tc::swz_off(row, col & ~7, rr()) + (uint32_t)(col & 7) * 2u;
+    __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
     if (PP == 4) {
-      __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
       __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
-      uint2 u;
-      u.x = *reinterpret_cast<uint32_t*>(&a);
-      u.y = *reinterpret_cast<uint32_t*>(&b);
-      *reinterpret_cast<uint2*>(p) = u;
+      tc::sts_v2_b32(p, *reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
     } else {
-      __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
-      *reinterpret_cast<__nv_bfloat162*>(p) = a;
+      tc::sts_b32(p, *reinterpret_cast<uint32_t*>(&a));
     }
   }
 
   template <int PP>
-  __device__ void st_lo(unsigned char* buf, int row, int col, const float* v) const {
+  __device__ void st_lo(uint32_t buf, int row, int col, const float* v) const {
     float lo[PP];
 #pragma unroll
     for (int j = 0; j < PP; ++j) lo[j] = v[j] - __bfloat162float(__float2bfloat16_rn(v[j]));
@@ -403,8 +408,8 @@ struct TcTile {
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          st_bf16<PPF>(ACT(out_buf), r, blk(c) * Pc + g, av[c]);
-          if (I.split3 && c >= TOP) st_lo<PPF>(ALO(out_buf), r, blk(c) * Pc + g, av[c]);
+          st_bf16<PPF>(act_s(out_buf), r, blk(c) * Pc + g, av[c]);
+          if (I.split3 && c >= TOP) st_lo<PPF>(alo_s(out_buf), r, blk(c) * Pc + g, av[c]);
         }
       }
     }
@@ -439,8 +444,8 @@ struct TcTile {
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          st_bf16<PPF>(ACT(out_buf), r, blk(c) * Pc + g, av[c]);
-          if (I.split3 && c >= TOP) st_lo<PPF>(ALO(out_buf), r, blk(c) * Pc + g, av[c]);
+          st_bf16<PPF>(act_s(out_buf), r, blk(c) * Pc + g, av[c]);
+          if (I.split3 && c >= TOP) st_lo<PPF>(alo_s(out_buf), r, blk(c) * Pc + g, av[c]);
         }
       }
     }
@@ -585,7 +590,7 @@ struct TcTile {
       for (int c = wg; c < C; c += nw())
         for (int q8 = 0; q8 < Pc; q8 += 8) {
           const int col = blk(c) * Pc + q8;
-          const uint4 raw = *reinterpret_cast<const uint4*>(ACT(a_buf) + tc::swz_off(r, col, rr()));
+          const uint4 raw = tc::lds_v4_b32(act_s(a_buf) + tc::swz_off(r, col, rr()));
           const __nv_bfloat16* bv = reinterpret_cast<const __nv_bfloat16*>(&raw);
           const float* ubc = ub + c * P + sub * Pc + q8;
 #pragma unroll
@@ -696,7 +701,7 @@ struct TcTile {
           gb += zb[0].v.y;
         }
 #pragma unroll
-        for (int c = 0; c < C; ++c) st_bf16<PPB>(ACT(z_buf), r, blk(c) * Pc + g, zbv[c]);
+        for (int c = 0; c < C; ++c) st_bf16<PPB>(act_s(z_buf), r, blk(c) * Pc + g, zbv[c]);
       }
       PART(wg, 0, r) = gb;
     }
