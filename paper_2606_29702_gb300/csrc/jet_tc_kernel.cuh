@@ -1046,7 +1046,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
   __shared__ uint32_t tmem_s;
   __shared__ volatile int abort_s;
   __shared__ double red_s[kTcThreads / 32];
-  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned base, derived from the shared array by pointer arithmetic
+  // only, so that every pointer computed from it is known to be shared
+  // (loads and stores through it compile to LDS / STS)
+  unsigned char* sm = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nthr = args.nthreads, nwg = nthr / 128;
   if (tid == 0) {
