@@ -369,6 +369,7 @@ struct TcTile {
   __device__ void layer1_fwd(int out_buf) {
     const float* Pm = I.params;
     const int Pc = pc();
+    const bool split3 = I.split3;
     constexpr int d = Cls::D;  // the plan's input dimension
     for (int h = 0; h < hh(); ++h) {
       const int r = h * 128 + ul;  // operand row
@@ -409,7 +410,7 @@ struct TcTile {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           st_bf16<PPF>(act_s(out_buf), r, blk(c) * Pc + g, av[c]);
-          if (I.split3 && c >= TOP) st_lo<PPF>(alo_s(out_buf), r, blk(c) * Pc + g, av[c]);
+          if (split3 && c >= TOP) st_lo<PPF>(alo_s(out_buf), r, blk(c) * Pc + g, av[c]);
         }
       }
     }
@@ -418,6 +419,7 @@ struct TcTile {
   // a^l = compose(D[R0] + b^l) -> ACT(out_buf)
   __device__ void hidden_epilogue(int l, int out_buf) {
     const int Pc = pc();
+    const bool split3 = I.split3;
     for (int h = 0; h < hh(); ++h) {
       const int r = h * 128 + ul;
       if (h * 128 + q * 32 >= ww()) continue;  // warp-uniform
@@ -445,7 +447,7 @@ struct TcTile {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           st_bf16<PPF>(act_s(out_buf), r, blk(c) * Pc + g, av[c]);
-          if (I.split3 && c >= TOP) st_lo<PPF>(alo_s(out_buf), r, blk(c) * Pc + g, av[c]);
+          if (split3 && c >= TOP) st_lo<PPF>(alo_s(out_buf), r, blk(c) * Pc + g, av[c]);
         }
       }
     }
@@ -642,8 +644,12 @@ struct TcTile {
     }
   }
 
-  // Zbar^l = (d compose/dz)^T Abar^l -> ACT(z_buf); db^l += sum_n Zbar_0
-  __device__ void adjoint_epilogue(int l, int z_buf, bool abar_from_ub) {
+  // Zbar^l = (d compose/dz)^T Abar^l -> ACT(z_buf); db^l += sum_n Zbar_0.
+  // Abar^l from TMEM (the data-gradient MMA), or for the last hidden layer
+  // from the output-layer adjoint ub (ABAR_FROM_UB): one instantiation each.
+  template <bool ABAR_FROM_UB>
+  __device__ void adjoint_epilogue(int l, int z_buf) {
+    constexpr bool abar_from_ub = ABAR_FROM_UB;
     const float* ub = UB();
     const int P = pp(), Pc = pc();
     for (int h = 0; h < hh(); ++h) {
@@ -982,7 +988,8 @@ struct TcTile {
       } else {
         if (!wait(bar_tma, ph_tma, 63)) break;  // W^{L-1} for the data gradient
       }
-      adjoint_epilogue(l, zb, l == L - 1);
+      if (l == L - 1) adjoint_epilogue<true>(l, zb);
+      else adjoint_epilogue<false>(l, zb);
       tc::fence_proxy_async_smem();
       sync();
       if (store) {
