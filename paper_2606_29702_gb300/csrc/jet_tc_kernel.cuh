@@ -380,7 +380,12 @@ struct TcTile {
       for (int i = 0; i < d; ++i) w1[i] = Pm[I.off_W[0] + u * d + i];
       const float b1 = Pm[I.off_b[0] + u];
       const float* xs = XS() + sub * Pc * d;
-      for (int g = wg * PPF; g < Pc; g += nw() * PPF) {
+      // the warpgroups split the points; a fixed shape makes the pass count a
+      // compile-time constant, so the passes unroll with constant offsets
+#pragma unroll
+      for (int k = 0; k < (Pc + nw() * PPF - 1) / (nw() * PPF); ++k) {
+        const int g = wg * PPF + k * nw() * PPF;
+        if (g >= Pc) break;
         float av[C][PPF];
 #pragma unroll
         for (int j = 0; j < PPF; j += 2) {
@@ -424,7 +429,12 @@ struct TcTile {
       const int r = h * 128 + ul;
       if (h * 128 + q * 32 >= ww()) continue;  // warp-uniform
       const float bu = I.params[I.off_b[l - 1] + r % wuu()];
-      for (int g = wg * PPF; g < Pc; g += nw() * PPF) {
+      // the warpgroups split the points; a fixed shape makes the pass count a
+      // compile-time constant, so the passes unroll with constant offsets
+#pragma unroll
+      for (int k = 0; k < (Pc + nw() * PPF - 1) / (nw() * PPF); ++k) {
+        const int g = wg * PPF + k * nw() * PPF;
+        if (g >= Pc) break;
         float zv[C][PPF];
 #pragma unroll
         for (int c = 0; c < C; ++c) tc::tmem_ld<PPF>(R0(h) + lane_base() + (uint32_t)(blk(c) * Pc + g), zv[c]);
@@ -665,7 +675,12 @@ struct TcTile {
           if (o < nout) wl[o] = I.params[I.off_W[I.L - 1] + (long long)o * wuu() + u];
       }
       float gb = 0.f;
-      for (int g = wg * PPB; g < Pc; g += nw() * PPB) {
+      // the warpgroups split the points; a fixed shape makes the pass count a
+      // compile-time constant, so the passes unroll with constant offsets
+#pragma unroll
+      for (int k = 0; k < (Pc + nw() * PPB - 1) / (nw() * PPB); ++k) {
+        const int g = wg * PPB + k * nw() * PPB;
+        if (g >= Pc) break;
         float zv[C][PPB], abv[C][PPB];
 #pragma unroll
         for (int c = 0; c < C; ++c) tc::tmem_ld<PPB>(R0(h) + lane_base() + (uint32_t)(blk(c) * Pc + g), zv[c]);
@@ -815,7 +830,12 @@ struct TcTile {
       float gw[d], gb = 0.f;
 #pragma unroll
       for (int i = 0; i < d; ++i) gw[i] = 0.f;
-      for (int g = wg * PPB; g < Pc; g += nw() * PPB) {
+      // the warpgroups split the points; a fixed shape makes the pass count a
+      // compile-time constant, so the passes unroll with constant offsets
+#pragma unroll
+      for (int k = 0; k < (Pc + nw() * PPB - 1) / (nw() * PPB); ++k) {
+        const int g = wg * PPB + k * nw() * PPB;
+        if (g >= Pc) break;
         float abv[C][PPB];
         if (!abar_from_ub) {
 #pragma unroll
