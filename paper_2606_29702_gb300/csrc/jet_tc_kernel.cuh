@@ -939,7 +939,11 @@ struct TcTile {
     for (int l = 2; l <= L - 1; ++l) {
       if (!wait(bar_tma, ph_tma, 10 + l)) break;
       if (tid == 0) {
-        tc::bulk_wait_read0();  // ACT(cur^1) is about to be rewritten
+        // ACT(cur^1) is about to be rewritten: its copy (two layers back) must
+        // have been read.  With two buffers, the newest group copies ACT(cur),
+        // which this layer's MMAs only read, and may stay in flight.
+        if (bwd && l - 1 <= last_a && I.o_a0 != I.o_a1) tc::bulk_wait_read1();
+        else tc::bulk_wait_read0();
         tc::tc_fence_after();
         mma_layer(cur);
         tc::mma_commit(bar_mma);
