@@ -661,8 +661,22 @@ void fill_tc(const jet_plan_s* p, const TcPlan* t, const void* params, const voi
   I.top_cols = t->top_cols;
   I.split3 = t->split3;
   I.n_terms = (int)p->terms.size();
-  for (int m = 0; m < I.n_terms; ++m) I.terms[m] = p->terms[m];
+  for (int m = 0; m < I.n_terms; ++m) {
+    I.terms[m] = p->terms[m];
+    I.coef_f[m] = (float)p->terms[m].coef;
+  }
   I.n_groups = p->n_groups > 0 ? jet::fill_groups(p, I.groups) : 0;
+  {  // per output-jet slot, the (monomial, factor) pairs that read it, in (m, f) order
+    int e = 0;
+    const int nslot = p->n_out * p->C;
+    for (int k = 0; k < nslot; ++k) {
+      I.adj_off[k] = (short)e;
+      for (int m = 0; m < I.n_terms; ++m)
+        for (int f = 0; f < I.terms[m].nfac; ++f)
+          if (I.terms[m].fac[f] == k) I.adj_mf[e++] = (unsigned char)(m * 4 + f);
+    }
+    I.adj_off[nslot] = (short)e;
+  }
   I.params = reinterpret_cast<const float*>(params);
   for (int l = 0; l < p->L; ++l) {
     I.off_W[l] = p->off_W[l];

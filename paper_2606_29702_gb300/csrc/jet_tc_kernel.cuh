@@ -106,6 +106,12 @@ struct alignas(64) TcInst {
   DevTerm terms[kMaxTerms];
   int n_groups;  // composite loss (0: one residual over all points)
   DevGroup groups[kMaxGroups];
+  // residual adjoint lists: for output-jet slot k (o * C + channel), the
+  // factors (monomial m, factor f) that read it, packed m * 4 + f, in (m, f)
+  // order at adj_mf[adj_off[k] .. adj_off[k + 1]); monomial coefficients in FP32
+  short adj_off[kMaxOut * kMaxC + 1];
+  unsigned char adj_mf[kMaxTerms * 4];
+  float coef_f[kMaxTerms];
   const float* params;
   long long off_W[kMaxLayers], off_b[kMaxLayers];
   long long n_params;
@@ -539,7 +545,7 @@ struct TcTile {
     for (int i = tid; i < nt * nvalid; i += nth()) {
       const int m = i / nvalid, n = i - m * nvalid;
       const DevTerm& tm = I.terms[m];
-      float prod = (float)tm.coef;
+      float prod = I.coef_f[m];
       for (int f = 0; f < tm.nfac; ++f) prod *= uo[tm.fac[f] * P + n];
       prodm[m * P + n] = prod;
     }
@@ -570,15 +576,13 @@ struct TcTile {
       const int k = i / P, n = i - k * P;
       float acc = 0.f;
       if (n < nvalid)
-        for (int m = 0; m < nt; ++m) {
+        for (int e = I.adj_off[k]; e < I.adj_off[k + 1]; ++e) {  // the factors reading slot k, in (m, f) order
+          const int m = I.adj_mf[e] >> 2, f = I.adj_mf[e] & 3;
           const DevTerm& tm = I.terms[m];
-          for (int f = 0; f < tm.nfac; ++f) {
-            if (tm.fac[f] != k) continue;
-            float prod = rg[tm.comp * P + n] * (float)tm.coef;
-            for (int q = 0; q < tm.nfac; ++q)
-              if (q != f) prod *= uo[tm.fac[q] * P + n];
-            acc += prod;
-          }
+          float prod = rg[tm.comp * P + n] * I.coef_f[m];
+          for (int q = 0; q < tm.nfac; ++q)
+            if (q != f) prod *= uo[tm.fac[q] * P + n];
+          acc += prod;
         }
       ub[i] = acc;
     }
