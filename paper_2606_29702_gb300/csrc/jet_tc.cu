@@ -159,11 +159,15 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_kernel(const __grid_const
                         tc::sdesc(as + (uint32_t)s * 32u, 16, 1024), id, (i > 0 || s > 0) ? 1u : 0u);
         tc::mma_commit(&empty[st]);
         pending[st] = true;
-        if (i + S < nch) {
-          if (!tc::mbar_wait(&empty[st], eph[st] & 1u, &abort_s, a.err, 72)) break;
-          ++eph[st];
-          pending[st] = false;
-          load(i + S, st);
+        // refill the previous chunk's stage once its MMAs (queued before this
+        // chunk's) are done: the tensor pipe keeps a chunk queued meanwhile
+        const long long j = i - 1;
+        if (j >= 0 && j + S < nch) {
+          const int sj = (int)(j % S);
+          if (!tc::mbar_wait(&empty[sj], eph[sj] & 1u, &abort_s, a.err, 72)) break;
+          ++eph[sj];
+          pending[sj] = false;
+          load(j + S, sj);
         }
       }
       for (int st = 0; st < S; ++st)
