@@ -201,6 +201,11 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
 # are scaled by the point count where the traffic is per tile (stated in the
 # profile summaries).
 TRAFFIC = {
+    # N = 65536 capture of both kernels (fused kernel + weight-gradient GEMM), x16
+    ("helmholtz_3x256x8", "bf16", "store"): ((629089280 + 3703625472 + 3760374272 + 107915008) * 16, "426af0e7fe54deea"),
+    ("ns_psi_3x128x6", "bf16", "tile"): (31503360 + 2472950272, "426af0e7fe54deea"),
+    ("ks_2x64x5", "bf16", "tile"): (857600 + 980224, "426af0e7fe54deea"),
+    ("ks_2x64x5", "fp32", "tile"): (7244032 + 819456512, "426af0e7fe54deea"),
 }
 
 
