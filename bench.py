@@ -206,6 +206,8 @@ TRAFFIC = {
     ("ns_psi_3x128x6", "bf16", "tile"): (31503360 + 2472950272, "426af0e7fe54deea"),
     ("ks_2x64x5", "bf16", "tile"): (857600 + 980224, "426af0e7fe54deea"),
     ("ks_2x64x5", "fp32", "tile"): (7244032 + 819456512, "426af0e7fe54deea"),
+    # the batched fused kernel of one ensemble step (the step is one graph replay)
+    ("ensemble_64", "bf16", "tile"): (635181824 + 2165030400, "426af0e7fe54deea"),
 }
 
 
