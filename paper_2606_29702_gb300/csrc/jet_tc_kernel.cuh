@@ -943,13 +943,15 @@ struct TcTile {
     for (int l = 2; l <= L - 1; ++l) {
       if (!wait(bar_tma, ph_tma, 10 + l)) break;
       if (tid == 0) {
-        // ACT(cur^1) is about to be rewritten: its copy (two layers back) must
-        // have been read.  With two buffers, the newest group copies ACT(cur),
-        // which this layer's MMAs only read, and may stay in flight.
-        if (bwd && l - 1 <= last_a && I.o_a0 != I.o_a1) tc::bulk_wait_read1();
-        else tc::bulk_wait_read0();
         tc::tc_fence_after();
         mma_layer(cur);
+        // This layer's epilogue rewrites ACT(cur^1) once the MMAs are complete:
+        // every copy that read it must be done reading before the commit that
+        // releases the epilogue.  With two buffers that is the copy two layers
+        // back (the newest copies ACT(cur), which the MMAs only read); with one
+        // buffer it is the newest, whose read overlaps the MMAs issued above.
+        if (bwd && l - 1 <= last_a && I.o_a0 != I.o_a1) tc::bulk_wait_read1();
+        else tc::bulk_wait_read0();
         tc::mma_commit(bar_mma);
       }
       if (!wait(bar_mma, ph_mma, 30 + l)) break;
@@ -993,9 +995,13 @@ struct TcTile {
     __syncthreads();  // PART is rewritten by the first adjoint epilogue
     const int zb = cur, ain = cur ^ 1;
     // thread 0: A^{l-1} and W^l for the recompute of layer l, requested as
-    // soon as the MMAs of layer l+1 have released both buffers
+    // soon as the MMAs of layer l+1 have released both buffers.  The layer
+    // inputs were written by this CTA's own bulk copies, which must be
+    // complete; the nz adjoint copies to the store committed after them may
+    // still be writing.
+    int nz = 0;
     auto request_reload = [&](int l) {
-      tc::bulk_wait0();
+      tc::bulk_wait_n(nz);
       tc::mbar_arrive_expect_tx(bar_ld, (uint32_t)(I.act_bytes + (I.split3 ? I.alo_bytes : 0)));
       scratch_in(ACT(ain), slot(l - 1), (uint32_t)I.act_bytes);
       if (I.split3) scratch_in(ALO(ain), slot(l - 1) + I.act_bytes, (uint32_t)I.alo_bytes);
@@ -1025,6 +1031,7 @@ struct TcTile {
         if (tid == 0) {
           tc::bulk_s2g(zslot(l), ACT(zb), (uint32_t)I.act_bytes);
           tc::bulk_commit();
+          ++nz;
           mma_dgrad(zb);
           tc::mma_commit(bar_mma);
         }
