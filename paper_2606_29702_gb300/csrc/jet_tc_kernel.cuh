@@ -196,10 +196,11 @@ struct TcTile {
   uint64_t* bar_tma;
   uint64_t* bar_mma;
   uint64_t* bar_ld;
+  uint64_t* bar_wg;  // the weight-gradient MMA of a backward layer (per-tile schedule)
   volatile int* abort_f;
   int* err;
   uint32_t tmem;
-  uint32_t ph_tma, ph_mma, ph_ld;
+  uint32_t ph_tma, ph_mma, ph_ld, ph_wg;
   int tid, warp;
   int R_;       // rows of every operand buffer (128 * H), for a runtime shape
   float* part;  // per-warpgroup partial sums [nwg][4][256]
@@ -1000,11 +1001,14 @@ struct TcTile {
     // complete; the nz adjoint copies to the store committed after them may
     // still be writing.
     int nz = 0;
-    auto request_reload = [&](int l) {
+    auto reload_act = [&](int l) {
       tc::bulk_wait_n(nz);
       tc::mbar_arrive_expect_tx(bar_ld, (uint32_t)(I.act_bytes + (I.split3 ? I.alo_bytes : 0)));
       scratch_in(ACT(ain), slot(l - 1), (uint32_t)I.act_bytes);
       if (I.split3) scratch_in(ALO(ain), slot(l - 1) + I.act_bytes, (uint32_t)I.alo_bytes);
+    };
+    auto request_reload = [&](int l) {
+      reload_act(l);
       load_hidden_w(l);
     };
     for (int l = L - 1; l >= 2; --l) {
@@ -1047,6 +1051,28 @@ struct TcTile {
       }
       const int NB = hh() == 2 ? 128 : ww();
       const int nblk = ww() / NB;
+      if (nblk == 1) {
+        // weight gradient first, with its own barrier: its flush from TMEM
+        // runs while the data-gradient MMA does, and A^{l-2} reloads into
+        // ACT(ain) as soon as the weight-gradient MMA has read A^{l-1}; W^{l-1}
+        // loads once the data-gradient MMA has read W^l
+        if (tid == 0) {
+          mma_wgrad(zb, ain, 0, NB);
+          tc::mma_commit(bar_wg);
+          mma_dgrad(zb);
+          tc::mma_commit(bar_mma);
+        }
+        part_flush(0, g + I.off_b[l - 1], 1);  // bias gradient of layer l, during the MMAs
+        if (!wait(bar_wg, ph_wg, 67)) break;
+        tc::tc_fence_after();
+        if (tid == 0 && l > 2) reload_act(l - 1);
+        acc_wgrad(l, 0, NB);
+        if (!wait(bar_mma, ph_mma, 64)) break;
+        tc::tc_fence_after();
+        if (tid == 0 && l > 2) load_hidden_w(l - 1);
+        sync();
+        continue;
+      }
       if (tid == 0) {
         mma_dgrad(zb);
         mma_wgrad(zb, ain, 0, NB);
@@ -1055,7 +1081,6 @@ struct TcTile {
       part_flush(0, g + I.off_b[l - 1], 1);  // bias gradient of layer l, during the MMAs
       if (!wait(bar_mma, ph_mma, 64)) break;
       tc::tc_fence_after();
-      if (tid == 0 && nblk == 1 && l > 2) request_reload(l - 1);
       acc_wgrad(l, 0, NB);
       for (int nb = 1; nb < nblk; ++nb) {
         sync();
@@ -1081,7 +1106,7 @@ struct TcTile {
 template <class Cls, class Shape>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant__ TcArgs args) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t bars[3];
+  __shared__ uint64_t bars[4];
   // the running work item's descriptor: every epilogue reads its fields, and
   // shared-memory loads keep those reads off the global/param path
   __shared__ TcInst inst_s;
@@ -1099,6 +1124,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
     tc::mbar_init(&bars[0], 1);
     tc::mbar_init(&bars[1], 1);
     tc::mbar_init(&bars[2], 1);
+    tc::mbar_init(&bars[3], 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -1108,7 +1134,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  uint32_t ph_tma = 0, ph_mma = 0, ph_ld = 0;
+  uint32_t ph_tma = 0, ph_mma = 0, ph_ld = 0, ph_wg = 0;
   int prev_inst = -1;
   for (int k = blockIdx.x; k < args.n_items && !abort_s; k += gridDim.x) {
     const int item = args.item_inst ? args.item_inst[k] : k;
@@ -1150,12 +1176,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
                   &bars[0],
                   &bars[1],
                   &bars[2],
+                  &bars[3],
                   &abort_s,
                   args.err,
                   tmem_s,
                   ph_tma,
                   ph_mma,
                   ph_ld,
+                  ph_wg,
                   tid,
                   warp,
                   128 * I.H,
@@ -1188,6 +1216,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
     ph_tma = T.ph_tma;
     ph_mma = T.ph_mma;
     ph_ld = T.ph_ld;
+    ph_wg = T.ph_wg;
     for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
     if ((tid & 31) == 0) red_s[warp] = loss;
     __syncthreads();
