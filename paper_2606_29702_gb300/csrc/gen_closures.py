@@ -121,7 +121,7 @@ for _i, (_d, _chans) in enumerate(_parse_extra(os.environ.get("JET_EXTRA_CLASSES
 # launch takes the first entry that matches, so exact shapes come first.
 FAST_SHAPES = {
     "burgers": [(64, 2, 1, 128, 512), (64, 0, 1, 128, 512)],  # width-64 nets (P = 128); ensembles, Pc = 64
-    "ks": [(40, 2, 1, 128, 512), (32, 2, 1, 128, 512), (16, 2, 1, 128, 256)],  # BF16 P = 80, BF16X3 P = 64, 2 CTAs P = 32
+    "ks": [(32, 2, 1, 128, 512), (40, 2, 1, 128, 512), (16, 2, 1, 128, 256)],  # BF16, BF16X3 P = 64, P = 80, 2 CTAs P = 32
     "helmholtz": [(16, 1, 2, 256, 512), (8, 1, 2, 256, 512)],  # 3->256x8->1: store P = 16, per tile P = 8
     "ns_psi": [(16, 1, 1, 128, 512), (8, 1, 1, 128, 512), (8, 1, 1, 128, 256)],  # BF16 16, BF16X3 8, 2 CTAs 8
     "ns_uvp": [(48, 2, 1, 128, 512)],                          # 2->64x6->3: P = 96

@@ -451,8 +451,9 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
   t->split3 = p->prec == JET_BF16X3 ? 1 : 0;
   const int ntop = C - top_begin;
   // choose the CTA shape and P: most points in flight per SM (P x CTAs per
-  // SM) within shared memory and TMEM (512 columns per SM); on a tie one CTA
-  // of 16 warps with the larger tile wins (measured faster than two CTAs of 8
+  // SM, doubled for tiles that give every warpgroup whole epilogue passes)
+  // within shared memory and TMEM (512 columns per SM); on a tie one CTA of
+  // 16 warps with the larger tile wins (measured faster than two CTAs of 8
   // warps with half the tile on the KS and NS workloads)
   int best_score = -1;
   TcPlan best = *t;
@@ -513,7 +514,11 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
         continue;
       }
       c.ctas_per_sm = ctas;
-      const int score = 2 * P * ctas + (ctas == 1 ? 1 : 0);
+      // the epilogues give each warpgroup passes of 4 points (up to 7
+      // channels) or 2: a tile that splits into whole passes counts double
+      const int pw = C <= 7 ? 4 : 2;
+      const bool whole = Pc % (pw * (c.nthreads / 128)) == 0;
+      const int score = 2 * P * ctas * (whole ? 2 : 1) + (ctas == 1 ? 1 : 0);
       if (score > best_score) {
         best_score = score;
         best = c;
