@@ -175,11 +175,12 @@ struct TcTile {
   static constexpr int NP = Cls::NP;
   static constexpr int TOP = Cls::TOP_BEGIN;
   // points per epilogue pass: four below seven channels (forward) or five
-  // (adjoint); up to seven channels, four where a compiled shape gives every
-  // warpgroup whole passes of four; two otherwise, so that small tiles keep
-  // every warpgroup busy and wide channel sets fit the registers
+  // (adjoint); four where a compiled shape gives every warpgroup whole
+  // passes of four (the adjoint only up to seven channels, where its three
+  // arrays of jets still fit the registers); two otherwise, so that small
+  // tiles keep every warpgroup busy
   static constexpr bool BAL4 = Shape::PC != 0 && Shape::NT != 0 && Shape::PC % (Shape::NT / 128 * 4) == 0;
-  static constexpr int PPF = C > 7 ? 2 : (C < 7 || BAL4) ? 4 : 2;
+  static constexpr int PPF = (C < 7 || BAL4) ? 4 : 2;
   static constexpr int PPB = (C < 5 || (C <= 7 && BAL4)) ? 4 : 2;
 
   // the tile shape: compile-time when the launch fixes it, else the descriptor's
