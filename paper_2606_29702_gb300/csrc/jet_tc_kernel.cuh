@@ -378,9 +378,46 @@ struct TcTile {
     st_bf16<PP>(buf, row, col, lo);
   }
 
+  // ------------------------------------------------------------ per-row parameters
+  // Parameters of this thread's operand rows (one per 128-row half), loaded
+  // ahead of the wait or barrier that precedes their epilogue, so that the
+  // global loads' latency hides behind it; compiled 256-wide shapes, whose
+  // registers are tighter (two row halves), load them in the epilogue.
+  static constexpr bool PRELOAD = Shape::H != 2;
+  struct RowBias {
+    float v[2];
+  };
+  __device__ RowBias row_bias(int l) const {  // b^l
+    RowBias b{};
+    if (!PRELOAD) return b;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = h * 128 + ul;
+      b.v[h] = (h < hh() && r < ww()) ? I.params[I.off_b[l - 1] + r % wuu()] : 0.f;
+    }
+    return b;
+  }
+  struct Row1 {  // W^1 and b^1
+    float w[2][Cls::D];
+    float b[2];
+  };
+  __device__ Row1 row_l1() const {
+    Row1 w{};
+    if (!PRELOAD) return w;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = h * 128 + ul;
+      const bool ok = h < hh() && r < ww();
+      const int u = r % wuu();
+#pragma unroll
+      for (int i = 0; i < Cls::D; ++i) w.w[h][i] = ok ? I.params[I.off_W[0] + u * Cls::D + i] : 0.f;
+      w.b[h] = ok ? I.params[I.off_b[0] + u] : 0.f;
+    }
+    return w;
+  }
+
   // ------------------------------------------------------------ forward pieces
-  __device__ void layer1_fwd(int out_buf) {
-    const float* Pm = I.params;
+  __device__ void layer1_fwd(int out_buf, const Row1& w1p) {
     const int Pc = pc();
     const bool split3 = I.split3;
     constexpr int d = Cls::D;  // the plan's input dimension
@@ -390,8 +427,8 @@ struct TcTile {
       const int sub = r / wuu(), u = r - sub * wuu();
       float w1[d];
 #pragma unroll
-      for (int i = 0; i < d; ++i) w1[i] = Pm[I.off_W[0] + u * d + i];
-      const float b1 = Pm[I.off_b[0] + u];
+      for (int i = 0; i < d; ++i) w1[i] = PRELOAD ? w1p.w[h][i] : I.params[I.off_W[0] + u * d + i];
+      const float b1 = PRELOAD ? w1p.b[h] : I.params[I.off_b[0] + u];
       const float* xs = XS() + sub * Pc * d;
       // the warpgroups split the points; a fixed shape makes the pass count a
       // compile-time constant, so the passes unroll with constant offsets
@@ -435,13 +472,13 @@ struct TcTile {
   }
 
   // a^l = compose(D[R0] + b^l) -> ACT(out_buf)
-  __device__ void hidden_epilogue(int l, int out_buf) {
+  __device__ void hidden_epilogue(int l, int out_buf, const RowBias& bias) {
     const int Pc = pc();
     const bool split3 = I.split3;
     for (int h = 0; h < hh(); ++h) {
       const int r = h * 128 + ul;
       if (h * 128 + q * 32 >= ww()) continue;  // warp-uniform
-      const float bu = I.params[I.off_b[l - 1] + r % wuu()];
+      const float bu = PRELOAD ? bias.v[h] : I.params[I.off_b[l - 1] + r % wuu()];
       // the warpgroups split the points; a fixed shape makes the pass count a
       // compile-time constant, so the passes unroll with constant offsets
 #pragma unroll
@@ -669,7 +706,7 @@ struct TcTile {
   // Abar^l from TMEM (the data-gradient MMA), or for the last hidden layer
   // from the output-layer adjoint ub (ABAR_FROM_UB): one instantiation each.
   template <bool ABAR_FROM_UB>
-  __device__ void adjoint_epilogue(int l, int z_buf) {
+  __device__ void adjoint_epilogue(int l, int z_buf, const RowBias& bias) {
     constexpr bool abar_from_ub = ABAR_FROM_UB;
     const float* ub = UB();
     const int P = pp(), Pc = pc();
@@ -677,7 +714,7 @@ struct TcTile {
       const int r = h * 128 + ul;
       if (h * 128 + q * 32 >= ww()) continue;
       const int sub = r / wuu(), u = r - sub * wuu();
-      const float bu = I.params[I.off_b[l - 1] + u];
+      const float bu = PRELOAD ? bias.v[h] : I.params[I.off_b[l - 1] + r % wuu()];
       const int nout = I.n_out;
       float wl[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
       if (abar_from_ub) {
@@ -924,6 +961,7 @@ struct TcTile {
     cur_tile = t;
     const bool store = bwd && I.wstore != nullptr;
     const int last_a = store ? L - 2 : L - 3;  // highest A^l copied out of shared memory
+    const Row1 w1 = row_l1();
     float* xs = XS();
     for (int i = tid; i < P * d; i += nth()) {
       const int n = i / d;
@@ -936,7 +974,7 @@ struct TcTile {
     }
     __syncthreads();
     // ---- forward
-    layer1_fwd(0);
+    layer1_fwd(0, w1);
     tc::fence_proxy_async_smem();
     sync();
     // scratch keeps A^l for l <= L-3 (A^{L-2} stays in shared memory for the
@@ -961,13 +999,14 @@ struct TcTile {
         else tc::bulk_wait_read0();
         tc::mma_commit(bar_mma);
       }
+      const RowBias bias = row_bias(l);
       if (!wait(bar_mma, ph_mma, 30 + l)) break;
       tc::tc_fence_after();
       if (tid == 0) {
         if (l + 1 <= L - 1) load_hidden_w(l + 1);
         else load_out_w();
       }
-      hidden_epilogue(l, cur ^ 1);
+      hidden_epilogue(l, cur ^ 1, bias);
       tc::fence_proxy_async_smem();
       sync();
       if (tid == 0 && bwd && l <= last_a) {
@@ -1018,6 +1057,7 @@ struct TcTile {
       load_hidden_w(l);
     };
     for (int l = L - 1; l >= 2; --l) {
+      const RowBias bias = row_bias(l);
       if (l < L - 1) {
         // recompute z^l = W^l A^{l-1} into R0
         if (!wait(bar_ld, ph_ld, 60)) break;
@@ -1032,8 +1072,8 @@ struct TcTile {
       } else {
         if (!wait(bar_tma, ph_tma, 63)) break;  // W^{L-1} for the data gradient
       }
-      if (l == L - 1) adjoint_epilogue<true>(l, zb);
-      else adjoint_epilogue<false>(l, zb);
+      if (l == L - 1) adjoint_epilogue<true>(l, zb, bias);
+      else adjoint_epilogue<false>(l, zb, bias);
       tc::fence_proxy_async_smem();
       sync();
       if (store) {
