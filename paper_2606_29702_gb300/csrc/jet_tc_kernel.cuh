@@ -598,7 +598,7 @@ struct TcTile {
       const int nres = I.n_res;
       float r[kMaxRes];
 #pragma unroll
-      for (int c = 0; c < kMaxRes; ++c) r[c] = (c < nres && I.source) ? -I.source[(n0 + n) * nres + c] : 0.f;
+      for (int c = 0; c < kMaxRes; ++c) r[c] = (c < nres && I.source) ? -ub[n * nres + c] : 0.f;  // source, staged
       for (int m = 0; m < nt; ++m) {
         const int cm = I.terms[m].comp;
         const float v = prodm[m * P + n];
@@ -967,6 +967,13 @@ struct TcTile {
       const int n = i / d;
       xs[i] = n < nvalid ? I.X[(n0 + n) * d + (i % d)] : 0.f;
     }
+    // the residual's source rows, staged in the output-adjoint area (free
+    // until the residual writes it) while the points load
+    if (I.source && I.n_groups == 0 && (I.n_terms + I.n_res) * P <= nw() * 4 * 256) {
+      float* ub = UB();
+      const int nr = I.n_res;
+      for (int i = tid; i < nvalid * nr; i += nth()) ub[i] = I.source[n0 * nr + i];
+    }
     if (tid == 0 && !*abort_f) {
       tc::bulk_wait_read0();  // earlier bulk stores must have read ACT(0) before it is rewritten
       if (L >= 3) load_hidden_w(2);
@@ -1089,8 +1096,9 @@ struct TcTile {
         if (!wait(bar_mma, ph_mma, 66)) break;
         tc::tc_fence_after();
         if (tid == 0) {
+          if (l > 2) load_hidden_w(l - 1);  // W^l is free: W^{l-1} loads while the copy reads
           tc::bulk_wait_read0();  // ACT(zb) is rewritten by the reload or the next adjoint
-          if (l > 2) request_reload(l - 1);
+          if (l > 2) reload_act(l - 1);
         }
         sync();
         continue;
