@@ -381,9 +381,13 @@ struct TcTile {
   // ------------------------------------------------------------ per-row parameters
   // Parameters of this thread's operand rows (one per 128-row half), loaded
   // ahead of the wait or barrier that precedes their epilogue, so that the
-  // global loads' latency hides behind it; compiled 256-wide shapes, whose
-  // registers are tighter (two row halves), load them in the epilogue.
-  static constexpr bool PRELOAD = Shape::H != 2;
+  // global loads' latency hides behind it.  Which ones pay was measured per
+  // shape class: the biases and the first layer's weights of the forward for
+  // 128-wide and packed shapes, the first layer's weights of the backward for
+  // 256-wide shapes (whose registers are tighter: two row halves).
+  static constexpr bool PRELOAD = Shape::H != 2;    // biases
+  static constexpr bool PRELOAD1 = Shape::H != 2;   // W^1, b^1 of the layer-1 forward
+  static constexpr bool PRELOAD1B = Shape::H == 2;  // W^1, b^1 of the layer-1 backward
   struct RowBias {
     float v[2];
   };
@@ -401,9 +405,9 @@ struct TcTile {
     float w[2][Cls::D];
     float b[2];
   };
-  __device__ Row1 row_l1() const {
+  __device__ Row1 row_l1(bool on) const {
     Row1 w{};
-    if (!PRELOAD) return w;
+    if (!on) return w;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int r = h * 128 + ul;
@@ -427,8 +431,8 @@ struct TcTile {
       const int sub = r / wuu(), u = r - sub * wuu();
       float w1[d];
 #pragma unroll
-      for (int i = 0; i < d; ++i) w1[i] = PRELOAD ? w1p.w[h][i] : I.params[I.off_W[0] + u * d + i];
-      const float b1 = PRELOAD ? w1p.b[h] : I.params[I.off_b[0] + u];
+      for (int i = 0; i < d; ++i) w1[i] = PRELOAD1 ? w1p.w[h][i] : I.params[I.off_W[0] + u * d + i];
+      const float b1 = PRELOAD1 ? w1p.b[h] : I.params[I.off_b[0] + u];
       const float* xs = XS() + sub * Pc * d;
       // the warpgroups split the points; a fixed shape makes the pass count a
       // compile-time constant, so the passes unroll with constant offsets
@@ -854,7 +858,7 @@ struct TcTile {
   }
 
   // layer-1 backward with z^1 recomputed from the points
-  __device__ void layer1_bwd(bool abar_from_ub) {
+  __device__ void layer1_bwd(bool abar_from_ub, const Row1& w1p) {
     const float* Pm = I.params;
     const float* ub = UB();
     const int P = pp(), Pc = pc();
@@ -865,8 +869,8 @@ struct TcTile {
       const int sub = r / wuu(), u = r - sub * wuu();
       float w1[d];
 #pragma unroll
-      for (int i = 0; i < d; ++i) w1[i] = Pm[I.off_W[0] + u * d + i];
-      const float b1 = Pm[I.off_b[0] + u];
+      for (int i = 0; i < d; ++i) w1[i] = PRELOAD1B ? w1p.w[h][i] : Pm[I.off_W[0] + u * d + i];
+      const float b1 = PRELOAD1B ? w1p.b[h] : Pm[I.off_b[0] + u];
       const int nout = I.n_out;
       float wl[kMaxOut] = {0.f, 0.f, 0.f, 0.f};
       if (abar_from_ub) {
@@ -961,7 +965,7 @@ struct TcTile {
     cur_tile = t;
     const bool store = bwd && I.wstore != nullptr;
     const int last_a = store ? L - 2 : L - 3;  // highest A^l copied out of shared memory
-    const Row1 w1 = row_l1();
+    const Row1 w1 = row_l1(PRELOAD1);
     float* xs = XS();
     for (int i = tid; i < P * d; i += nth()) {
       const int n = i / d;
@@ -1063,6 +1067,7 @@ struct TcTile {
       reload_act(l);
       load_hidden_w(l);
     };
+    Row1 w1b;  // W^1, b^1 for the layer-1 backward, loaded before the last MMA wait
     for (int l = L - 1; l >= 2; --l) {
       const RowBias bias = row_bias(l);
       if (l < L - 1) {
@@ -1093,6 +1098,7 @@ struct TcTile {
           tc::mma_commit(bar_mma);
         }
         part_flush(0, g + I.off_b[l - 1], 1);  // bias gradient of layer l, during the MMA
+        if (l == 2) w1b = row_l1(PRELOAD1B);
         if (!wait(bar_mma, ph_mma, 66)) break;
         tc::tc_fence_after();
         if (tid == 0) {
@@ -1121,6 +1127,7 @@ struct TcTile {
         tc::tc_fence_after();
         if (tid == 0 && l > 2) reload_act(l - 1);
         acc_wgrad(l, 0, NB);
+        if (l == 2) w1b = row_l1(PRELOAD1B);
         if (!wait(bar_mma, ph_mma, 64)) break;
         tc::tc_fence_after();
         if (tid == 0 && l > 2) load_hidden_w(l - 1);
@@ -1133,6 +1140,7 @@ struct TcTile {
         tc::mma_commit(bar_mma);
       }
       part_flush(0, g + I.off_b[l - 1], 1);  // bias gradient of layer l, during the MMAs
+      if (l == 2) w1b = row_l1(PRELOAD1B);
       if (!wait(bar_mma, ph_mma, 64)) break;
       tc::tc_fence_after();
       acc_wgrad(l, 0, NB);
@@ -1149,7 +1157,8 @@ struct TcTile {
       }
       sync();
     }
-    if (!*abort_f) layer1_bwd(L == 2);
+    if (L == 2) w1b = row_l1(PRELOAD1B);
+    if (!*abort_f) layer1_bwd(L == 2, w1b);
     sync();
     if (!*abort_f) layer1_flush(g);
     __syncthreads();
