@@ -1,5 +1,7 @@
 // Weight transposition (plus an aligned copy of the parameters), deterministic FP64 gradient/loss reduction over the
 // chunk slices, and the fused full-batch Adam update (Sec. 3.1.1).
+#include <cmath>
+
 #include "jet_internal.h"
 
 namespace jet {
@@ -38,10 +40,12 @@ cudaError_t launch_transpose_weights(const DevInstance& in, bool fp64, void* Wt,
 // type of the parameters (FP32 for the FP32 and BF16 forms); the gradient it
 // takes is the FP64 sum over chunks.
 // The 1-based step t is `step`, or *step_ctr + 1 when the counter lives in
-// device memory; the bias corrections 1 - beta^t are formed on the device in
-// both cases, so the two give identical updates for the same t.
+// device memory; the bias corrections 1 - beta^t = -expm1(t ln beta) are
+// formed on the device in both cases (ln beta from the host), so the two give
+// identical updates for the same t.
 struct AdamConst {
   double lr, beta1, beta2, eps;
+  double ln_beta1, ln_beta2;
   float lr_f, beta1_f, beta2_f, eps_f;
   long long step;
   const long long* step_ctr;
@@ -57,16 +61,25 @@ template <class T, bool ADAM>
 __global__ void __launch_bounds__(32 * kRedWarps) reduce_kernel(const __grid_constant__ ReduceJob job0,
                                                                 const ReduceJob* jobs, AdamConst ac) {
   const ReduceJob& J = jobs ? jobs[blockIdx.y] : job0;
+  // the grid covers the largest job: blocks past this job's parameters have
+  // nothing to do (block 0 stays: it writes the loss, also of loss-only jobs)
+  if (blockIdx.x > 0 && (long long)blockIdx.x * 32 >= J.n_params) return;
   __shared__ double part[kRedWarps][32];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int gc = J.grad_chunks > 0 ? J.grad_chunks : J.n_chunks;
-  // bias corrections: one thread per block (FP64 pow is slow on this GPU)
+  // bias corrections: one thread per block, one expm1 each (FP32 for the
+  // FP32 update; FP64 arithmetic is slow on this GPU)
   __shared__ double bc_s[2];
   if (ADAM) {
     if (threadIdx.x == 0) {
       const long long t = ac.step_ctr ? *ac.step_ctr + 1 : ac.step;
-      bc_s[0] = 1.0 - pow(ac.beta1, (double)t);
-      bc_s[1] = 1.0 - pow(ac.beta2, (double)t);
+      if (sizeof(T) == 4) {
+        bc_s[0] = (double)-expm1f((float)((double)t * ac.ln_beta1));
+        bc_s[1] = (double)-expm1f((float)((double)t * ac.ln_beta2));
+      } else {
+        bc_s[0] = -expm1((double)t * ac.ln_beta1);
+        bc_s[1] = -expm1((double)t * ac.ln_beta2);
+      }
     }
     __syncthreads();
   }
@@ -124,6 +137,8 @@ cudaError_t launch_reduce(const ReduceJob* dev_jobs, const ReduceJob& job0, int 
   ac.beta1 = 0.9;
   ac.beta2 = 0.999;
   ac.eps = 1e-8;
+  ac.ln_beta1 = std::log(ac.beta1);
+  ac.ln_beta2 = std::log(ac.beta2);
   ac.lr_f = lr;
   ac.beta1_f = 0.9f;
   ac.beta2_f = 0.999f;
