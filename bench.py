@@ -202,12 +202,12 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
 # profile summaries).
 TRAFFIC = {
     # N = 65536 capture of both kernels (fused kernel + weight-gradient GEMM), x16
-    ("helmholtz_3x256x8", "bf16", "store"): ((629089280 + 3703625472 + 3760374272 + 107915008) * 16, "426af0e7fe54deea"),
-    ("ns_psi_3x128x6", "bf16", "tile"): (31503360 + 2472950272, "426af0e7fe54deea"),
-    ("ks_2x64x5", "bf16", "tile"): (857600 + 980224, "426af0e7fe54deea"),
-    ("ks_2x64x5", "fp32", "tile"): (7244032 + 819456512, "426af0e7fe54deea"),
+    ("helmholtz_3x256x8", "bf16", "store"): ((627284224 + 3770637568 + 3760838144 + 109966848) * 16, "675b996392eac08e"),
+    ("ns_psi_3x128x6", "bf16", "tile"): (20785152 + 2449118720, "675b996392eac08e"),
+    ("ks_2x64x5", "bf16", "tile"): (851200 + 941056, "675b996392eac08e"),
+    ("ks_2x64x5", "fp32", "tile"): (14127872 + 809962496, "675b996392eac08e"),
     # the batched fused kernel of one ensemble step (the step is one graph replay)
-    ("ensemble_64", "bf16", "tile"): (635181824 + 2165030400, "426af0e7fe54deea"),
+    ("ensemble_64", "bf16", "tile"): (621953792 + 2138414080, "675b996392eac08e"),
 }
 
 
