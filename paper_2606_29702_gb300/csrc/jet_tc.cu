@@ -577,7 +577,16 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
     t->wstore_budget = mem_budget;
     if ((long long)(mem_budget / (size_t)t->wstore_tile_stride) > 0) {
       t->wg_sms = prop.multiProcessorCount;
-      const int ipl = std::max(1, (2 * t->wg_sms + L - 3) / (L - 2));
+      // items of equal size, (L - 2) * ipl of them a multiple of the CTAs, so
+      // that every CTA takes the same number (no tail of a few CTAs running
+      // one more item): ipl = wg_sms / gcd(wg_sms, L - 2)
+      int a = t->wg_sms, b = L - 2;
+      while (b) {
+        const int r = a % b;
+        a = b;
+        b = r;
+      }
+      const int ipl = std::max(1, t->wg_sms / a);
       t->wg_max_items = (L - 2) * ipl;
       const size_t b_wo = (size_t)t->wg_max_items * t->w * t->w * sizeof(double);
       e = cudaMalloc((void**)&t->wg_out, b_wo);
