@@ -973,6 +973,7 @@ struct TcBatch {
   TcInst* h_insts = nullptr;
   int* d_items = nullptr;
   int* h_items = nullptr;
+  int* d_next = nullptr;  // the kernel's item counter
   ReduceJob* d_jobs = nullptr;
   ReduceJob* h_jobs = nullptr;
   PrepJob* d_prep = nullptr;  // weight preparation of every member, one launch
@@ -1023,6 +1024,7 @@ jet_status tc_batch_create(const std::vector<jet_plan_s*>& plans, TcBatch** out)
   e = cudaMalloc((void**)&b->d_insts, sizeof(TcInst) * b->n);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_insts, sizeof(TcInst) * b->n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, sizeof(int) * 2 * b->max_items);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_next, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_items, sizeof(int) * 2 * b->max_items);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_jobs, sizeof(ReduceJob) * b->n);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_jobs, sizeof(ReduceJob) * b->n);
@@ -1049,6 +1051,7 @@ void tc_batch_destroy(TcBatch* b) {
   cudaFree(b->d_insts);
   cudaFreeHost(b->h_insts);
   cudaFree(b->d_items);
+  cudaFree(b->d_next);
   cudaFreeHost(b->h_items);
   cudaFree(b->d_jobs);
   cudaFreeHost(b->h_jobs);
@@ -1163,10 +1166,13 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
   a.n_items = base;
   a.insts = b->d_insts;
   a.item_inst = b->d_items;
+  a.item_next = b->d_next;
   a.err = b->err;
   a.tmem_cols = b->tmem_cols;
   a.nthreads = b->nthreads;
-  cudaError_t e = tc_launch(b->cls, a, std::min(b->grid, base), b->smem, s);
+  cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(int), s);
+  if (e != cudaSuccess) return tcuda(e, "batch item counter reset");
+  e = tc_launch(b->cls, a, std::min(b->grid, base), b->smem, s);
   if (e != cudaSuccess) return tcuda(e, "batched tc kernel launch");
   long long maxp = 0;
   bool jobs_same = !capturing;

@@ -156,6 +156,10 @@ struct TcArgs {
   int* err;
   int tmem_cols;
   int nthreads;  // launch block size: 256 or 512
+  // batches: counter of the items taken after each CTA's first (zeroed before
+  // the launch); a CTA that finishes an item takes the next in the
+  // cost-ordered list, so the work balances itself.  Null: a fixed stride.
+  int* item_next;
 };
 
 // Tile shape of a launch: points per sub-tile PC, packed sub-tiles G, 128-row
@@ -1199,7 +1203,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
   tc::tc_fence_after();
   uint32_t ph_tma = 0, ph_mma = 0, ph_ld = 0, ph_wg = 0;
   int prev_inst = -1;
-  for (int k = blockIdx.x; k < args.n_items && !abort_s; k += gridDim.x) {
+  __shared__ int k_s;
+  for (int k = blockIdx.x; k < args.n_items && !abort_s;) {
     const int item = args.item_inst ? args.item_inst[k] : k;
     const int ii = args.insts ? args.item_inst[args.n_items + item] : 0;
     const TcInst& Ig = args.insts ? args.insts[ii] : args.inst0;
@@ -1287,6 +1292,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
       double s = 0.0;
       for (int w = 0; w < nthr / 32; ++w) s += red_s[w];
       I.loss_slices[chunk] = s;
+    }
+    // the next item: from the shared counter, or a fixed stride
+    if (args.item_next) {
+      if (tid == 0) k_s = (int)gridDim.x + atomicAdd(args.item_next, 1);
+      __syncthreads();
+      k = k_s;
+    } else {
+      k += gridDim.x;
     }
     __syncthreads();
   }
