@@ -717,6 +717,7 @@ struct jet_batch_s {
   // device workspace
   DevInstance* d_insts = nullptr;
   int* d_item_inst = nullptr;
+  int* d_next = nullptr;  // the kernel's item counter
   ReduceJob* d_jobs = nullptr;
   double* grad_slices = nullptr;
   double* loss_slices = nullptr;
@@ -741,6 +742,7 @@ namespace {
 void free_batch(jet_batch_s* b) {
   cudaFree(b->d_insts);
   cudaFree(b->d_item_inst);
+  cudaFree(b->d_next);
   cudaFree(b->d_jobs);
   cudaFree(b->grad_slices);
   cudaFree(b->loss_slices);
@@ -865,6 +867,7 @@ jet_status jet_batch_create(jet_batch_t* out, int32_t n, const jet_plan_t* plans
   const size_t elem = b->fp64 ? 8 : 4;
   e = cudaMalloc((void**)&b->d_insts, sizeof(DevInstance) * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_item_inst, sizeof(int) * 2 * b->max_items);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_next, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_jobs, sizeof(ReduceJob) * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->grad_slices, sizeof(double) * std::max<long long>(slices, 1));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->loss_slices, sizeof(double) * b->max_items);
@@ -900,6 +903,8 @@ static jet_status batch_run(jet_batch_t b, const void* const* params, void* cons
   a.item_inst = b->d_item_inst;
   a.scratch = b->scratch;
   a.scratch_stride = b->scratch_stride;
+  a.item_next = b->d_next;
+  CK(cudaMemsetAsync(b->d_next, 0, sizeof(int), s));
   CK(simt_launch(b->cls, b->fp64, a, std::min(b->grid, n_items), b->smem, s));
   long long maxp = 0;
   for (int i = 0; i < n; ++i) {

@@ -95,6 +95,10 @@ struct SimtArgs {
   const int* item_inst;       // [n_items] instance of each item (batched) or null
   void* scratch;              // per-CTA z-jet scratch
   long long scratch_stride;   // elements per CTA slot
+  // batches: counter of the items taken after each CTA's first (zeroed before
+  // the launch), so that a CTA that finishes takes the next item of the
+  // cost-ordered list; null: a fixed stride
+  int* item_next;
 };
 
 constexpr int kSimtThreads = 256;

@@ -777,7 +777,8 @@ constexpr int kWaccTiles = 64;  // tiles per FP32 weight-gradient run (FP32 form
 template <class Cls, class T>
 __device__ __forceinline__ void simt_body(const SimtArgs& args) {
   extern __shared__ __align__(16) unsigned char smem[];
-  for (int k = blockIdx.x; k < args.n_items; k += gridDim.x) {
+  __shared__ int k_s;
+  for (int k = blockIdx.x; k < args.n_items;) {
     // batched launches walk a cost-ordered list: position k -> item id, and
     // item id -> instance (second half of item_inst)
     const int item = args.item_inst ? args.item_inst[k] : k;
@@ -841,6 +842,14 @@ __device__ __forceinline__ void simt_body(const SimtArgs& args) {
       double s = 0.0;
       for (int w = 0; w < kSimtThreads / 32; ++w) s += S.RED[w];
       I.loss_slices[chunk] = s;
+    }
+    // the next item: from the shared counter, or a fixed stride
+    if (args.item_next) {
+      if (threadIdx.x == 0) k_s = (int)gridDim.x + atomicAdd(args.item_next, 1);
+      __syncthreads();
+      k = k_s;
+    } else {
+      k += gridDim.x;
     }
     __syncthreads();
   }
