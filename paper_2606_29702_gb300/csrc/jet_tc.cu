@@ -1088,8 +1088,9 @@ jet_status tc_batch_run(TcBatch* bb, const std::vector<jet_plan_s*>& plans, cons
     prep_jobs[i] = prep_job(plans[i], plans[i]->tcp, params[i], prep_total);
     prep_total += prep_jobs[i].nh + prep_jobs[i].nl;
   }
-  // work list: about four items per CTA, cost-ordered, largest first
-  const long long target = std::max<long long>(1, (total_tiles + 4LL * b->grid - 1) / (4LL * b->grid));
+  // work list: about eight items per CTA, cost-ordered, largest first (CTAs take
+  // them from a shared counter, so the smaller ones fill the tail)
+  const long long target = std::max<long long>(1, (total_tiles + 8LL * b->grid - 1) / (8LL * b->grid));
   std::vector<TcInst> insts(n);
   std::vector<std::pair<double, int>> cost;
   std::vector<int> inst_of;
