@@ -201,13 +201,14 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
 # are scaled by the point count where the traffic is per tile (stated in the
 # profile summaries).
 TRAFFIC = {
-    # N = 65536 capture of both kernels (fused kernel + weight-gradient GEMM), x16
-    ("helmholtz_3x256x8", "bf16", "store"): ((627284224 + 3770637568 + 3760838144 + 109966848) * 16, "675b996392eac08e"),
-    ("ns_psi_3x128x6", "bf16", "tile"): (20785152 + 2449118720, "675b996392eac08e"),
-    ("ks_2x64x5", "bf16", "tile"): (851200 + 941056, "675b996392eac08e"),
-    ("ks_2x64x5", "fp32", "tile"): (14127872 + 809962496, "675b996392eac08e"),
+    # N = 65536 capture of both kernels (fused kernel + weight-gradient GEMM): the store's bytes x16; the GEMM's
+    # per-item FP64 partials (one per CTA and layer, the same at any N) once
+    ("helmholtz_3x256x8", "bf16", "store"): ((624791808 + 3770373888 + 3764486912) * 16 + 502662144, "41d7f8cb3ba0849d"),
+    ("ns_psi_3x128x6", "bf16", "tile"): (21027072 + 2452067840, "41d7f8cb3ba0849d"),
+    ("ks_2x64x5", "bf16", "tile"): (852480 + 948480, "41d7f8cb3ba0849d"),
+    ("ks_2x64x5", "fp32", "tile"): (14286848 + 813100544, "41d7f8cb3ba0849d"),
     # the batched fused kernel of one ensemble step (the step is one graph replay)
-    ("ensemble_64", "bf16", "tile"): (621953792 + 2138414080, "675b996392eac08e"),
+    ("ensemble_64", "bf16", "tile"): (856785664 + 2870396672, "41d7f8cb3ba0849d"),
 }
 
 
