@@ -348,8 +348,8 @@ jet_status jet_plan_profile_read(jet_plan_t plan, int64_t* launches, double* tot
  * Shapes whose working set exceeds 8 MiB even with a single chunk of tiles
  * are rejected with JET_ERR_UNSUPPORTED before any launch.
  * Set-up: the first call on each device looks up the array's device address
- * with cudaGetSymbolAddress (that device current); make that first call
- * before any stream capture.  Every call reuses the same array and leaves its
+ * with cudaGetSymbolAddress (that device current) and caches it for the
+ * later calls on that device.  Every call reuses the same array and leaves its
  * contents behind; each call writes every part it reads, so nothing has to be
  * cleared, but calls that overlap on the GPU (two streams or two host
  * threads) race on the array and must be serialised by the caller.
