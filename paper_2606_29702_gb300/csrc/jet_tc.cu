@@ -63,7 +63,7 @@ struct TcPlan {
   unsigned char* wstore = nullptr;
   long long wstore_tile_stride = 0, wstore_tiles = 0;
   size_t wstore_budget = 0;  // grown on demand up to this many bytes
-  double* wg_out = nullptr;  // [max_items][w*w]
+  float* wg_out = nullptr;  // [max_items][w*w]
   int wg_max_items = 0, wg_sms = 0;
 };
 
@@ -75,7 +75,8 @@ constexpr double kSliceBudgetBytes = 48.0 * 1024 * 1024;
 // Wbar^l = sum over the tiles of a K range of Zbar^l A^{l-1}^T, both operands
 // read from the store in the fused kernel's swizzled layout, 64 columns
 // (one layout chunk) per pipeline stage; the accumulator stays in TMEM for
-// the whole range and is written once, in FP64, to the item's partial.
+// the whole range and is written once to the item's partial, in FP32 (its own
+// precision: the FP64 sum over the items reads the same values).
 struct WgArgs {
   const unsigned char* wstore;
   long long tile_stride;  // bytes per tile in the store
@@ -86,7 +87,7 @@ struct WgArgs {
   long long n_tiles;
   int items_per_layer, n_items;
   long long tiles_per_item;
-  double* out;
+  float* out;
   int* err;
   int tmem_cols;
 };
@@ -118,7 +119,8 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_kernel(const __grid_const
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = tmem_s;
-  uint32_t fph[kWgMaxStages] = {0, 0, 0, 0}, eph[kWgMaxStages] = {0, 0, 0, 0}, dph = 0;
+  // phase parities of the full / empty barriers, one bit per stage (registers, not a local array)
+  uint32_t fph = 0, eph = 0, dph = 0;
   const int ww = a.w * a.w;
   const uint32_t id = tc::idesc_bf16(128, a.w, 0, 0);
   for (int item = blockIdx.x; item < a.n_items && !abort_s; item += gridDim.x) {
@@ -126,13 +128,13 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_kernel(const __grid_const
     const long long t0 = (long long)(item % a.items_per_layer) * a.tiles_per_item;
     const long long t1 = t0 + a.tiles_per_item < a.n_tiles ? t0 + a.tiles_per_item : a.n_tiles;
     const long long nch = t1 > t0 ? (t1 - t0) * a.ach : 0;
-    double* out = a.out + (long long)item * ww;
+    float* out = a.out + (long long)item * ww;
     if (nch == 0) {
-      for (int i = tid; i < ww; i += kWgThreads) out[i] = 0.0;
+      for (int i = tid; i < ww; i += kWgThreads) out[i] = 0.f;
       continue;
     }
     if (tid == 0) {
-      bool pending[kWgMaxStages] = {false, false, false, false};
+      uint32_t pending = 0;  // stages whose MMAs are not yet known complete, one bit each
       auto load = [&](long long i, int st) {
         const long long t = t0 + i / a.ach;
         const int cc = (int)(i % a.ach);
@@ -148,8 +150,8 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_kernel(const __grid_const
       for (long long i = 0; i < S && i < nch; ++i) load(i, (int)i);
       for (long long i = 0; i < nch && !abort_s; ++i) {
         const int st = (int)(i % S);
-        if (!tc::mbar_wait(&full[st], fph[st] & 1u, &abort_s, a.err, 71)) break;
-        ++fph[st];
+        if (!tc::mbar_wait(&full[st], (fph >> st) & 1u, &abort_s, a.err, 71)) break;
+        fph ^= 1u << st;
         tc::tc_fence_after();
         const uint32_t zs = tc::smem_u32(sm + (size_t)st * 2 * a.chunk_bytes);
         const uint32_t as = zs + (uint32_t)a.chunk_bytes;
@@ -158,22 +160,22 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_kernel(const __grid_const
             tc::mma_f16(tmem + (uint32_t)(h * a.w), tc::sdesc(zs + (uint32_t)h * 16384u + (uint32_t)s * 32u, 16, 1024),
                         tc::sdesc(as + (uint32_t)s * 32u, 16, 1024), id, (i > 0 || s > 0) ? 1u : 0u);
         tc::mma_commit(&empty[st]);
-        pending[st] = true;
+        pending |= 1u << st;
         // refill the previous chunk's stage once its MMAs (queued before this
         // chunk's) are done: the tensor pipe keeps a chunk queued meanwhile
         const long long j = i - 1;
         if (j >= 0 && j + S < nch) {
           const int sj = (int)(j % S);
-          if (!tc::mbar_wait(&empty[sj], eph[sj] & 1u, &abort_s, a.err, 72)) break;
-          ++eph[sj];
-          pending[sj] = false;
+          if (!tc::mbar_wait(&empty[sj], (eph >> sj) & 1u, &abort_s, a.err, 72)) break;
+          eph ^= 1u << sj;
+          pending &= ~(1u << sj);
           load(j + S, sj);
         }
       }
       for (int st = 0; st < S; ++st)
-        if (pending[st]) {
-          tc::mbar_wait(&empty[st], eph[st] & 1u, &abort_s, a.err, 73);
-          ++eph[st];
+        if ((pending >> st) & 1u) {
+          tc::mbar_wait(&empty[st], (eph >> st) & 1u, &abort_s, a.err, 73);
+          eph ^= 1u << st;
         }
       tc::mma_commit(&done);
     }
@@ -182,13 +184,29 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_kernel(const __grid_const
     tc::tc_fence_after();
     for (int h = 0; h < a.H; ++h) {
       const int row = h * 128 + tid;
-      for (int k0 = 0; k0 < a.w; k0 += 8) {
-        float v[8];
-        tc::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * a.w + k0), v);
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * a.w);
+      float* orow = out + (long long)row * a.w;
+      int k0 = 0;
+      // four loads of 8 columns in flight per wait, 128-byte row segments out
+      for (; k0 + 32 <= a.w; k0 += 32) {
+        float v[32];
+        tc::tmem_ld8(ta + (uint32_t)k0, v);
+        tc::tmem_ld8(ta + (uint32_t)(k0 + 8), v + 8);
+        tc::tmem_ld8(ta + (uint32_t)(k0 + 16), v + 16);
+        tc::tmem_ld8(ta + (uint32_t)(k0 + 24), v + 24);
         tc::tmem_wait_ld();
         if (row < a.w)
 #pragma unroll
-          for (int i = 0; i < 8; ++i) out[(long long)row * a.w + k0 + i] = (double)v[i];
+          for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<float4*>(orow + k0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      }
+      for (; k0 < a.w; k0 += 8) {
+        float v[8];
+        tc::tmem_ld8(ta + (uint32_t)k0, v);
+        tc::tmem_wait_ld();
+        if (row < a.w)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) orow[k0 + i] = v[i];
       }
     }
     tc::tc_fence_before();
@@ -208,16 +226,23 @@ struct OffWl {
   long long v[kMaxLayers];
 };
 
-__global__ void wgrad_sum_kernel(const double* out, int L, int w, int wu, int G, int ipl, OffWl offW, double* dst) {
+// (offW is a __grid_constant__: read in place, not copied to local memory for the runtime index)
+__global__ void wgrad_sum_kernel(const float* out, int L, int w, int wu, int G, int ipl,
+                                 const __grid_constant__ OffWl offW, double* dst) {
   const long long ww = (long long)w * w, uu = (long long)wu * wu, total = (long long)(L - 2) * uu;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int li = (int)(e / uu);
     const long long r = e % uu;
     const int i = (int)(r / wu), k = (int)(r % wu);
+    const float* src = out + (long long)li * ipl * ww;
     double s = 0.0;
-    for (int it = 0; it < ipl; ++it)
-      for (int b = 0; b < G; ++b) s += out[((long long)li * ipl + it) * ww + (long long)(b * wu + i) * w + b * wu + k];
+    for (int b = 0; b < G; ++b) {
+      const long long o = (long long)(b * wu + i) * w + b * wu + k;
+      // the item partials in a fixed order; the loads of eight items issue together
+#pragma unroll 8
+      for (int it = 0; it < ipl; ++it) s += (double)src[it * ww + o];
+    }
     dst[offW.v[li + 1] + r] += s;
   }
 }
@@ -588,7 +613,7 @@ jet_status tc_plan_create(jet_plan_s* p, TcPlan** out, const cudaDeviceProp& pro
       }
       const int ipl = std::max(1, t->wg_sms / a);
       t->wg_max_items = (L - 2) * ipl;
-      const size_t b_wo = (size_t)t->wg_max_items * t->w * t->w * sizeof(double);
+      const size_t b_wo = (size_t)t->wg_max_items * t->w * t->w * sizeof(float);
       e = cudaMalloc((void**)&t->wg_out, b_wo);
       if (e != cudaSuccess) {
         tc_plan_destroy(t);
