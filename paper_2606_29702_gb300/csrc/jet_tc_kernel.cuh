@@ -1109,6 +1109,8 @@ struct TcTile {
           if (l > 2) load_hidden_w(l - 1);  // W^l is free: W^{l-1} loads while the copy reads
           tc::bulk_wait_read0();  // ACT(zb) is rewritten by the reload or the next adjoint
           if (l > 2) reload_act(l - 1);
+          // the layer input of the next reload, from HBM into L2 a layer ahead
+          if (l > 3) tc::bulk_prefetch_l2(slot(l - 3), (uint32_t)I.act_bytes);
         }
         sync();
         continue;
