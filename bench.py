@@ -202,13 +202,13 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
 # profile summaries).
 TRAFFIC = {
     # N = 65536 capture of both kernels (fused kernel + weight-gradient GEMM): the store's bytes x16; the GEMM's
-    # per-item FP64 partials (one per CTA and layer, the same at any N) once
-    ("helmholtz_3x256x8", "bf16", "store"): ((624791808 + 3770373888 + 3764486912) * 16 + 502662144, "41d7f8cb3ba0849d"),
-    ("ns_psi_3x128x6", "bf16", "tile"): (21027072 + 2452067840, "41d7f8cb3ba0849d"),
-    ("ks_2x64x5", "bf16", "tile"): (852480 + 948480, "41d7f8cb3ba0849d"),
-    ("ks_2x64x5", "fp32", "tile"): (14286848 + 813100544, "41d7f8cb3ba0849d"),
+    # per-item FP32 partials (one per CTA and layer, the same at any N) once
+    ("helmholtz_3x256x8", "bf16", "store"): ((643409408 + 3771733760 + 3758907136) * 16 + 240279040, "d8b350db0c17d40c"),
+    ("ns_psi_3x128x6", "bf16", "tile"): (35178752 + 2482989568, "d8b350db0c17d40c"),
+    ("ks_2x64x5", "bf16", "tile"): (851968 + 879104, "d8b350db0c17d40c"),
+    ("ks_2x64x5", "fp32", "tile"): (13456896 + 813855488, "d8b350db0c17d40c"),
     # the batched fused kernel of one ensemble step (the step is one graph replay)
-    ("ensemble_64", "bf16", "tile"): (856785664 + 2870396672, "41d7f8cb3ba0849d"),
+    ("ensemble_64", "bf16", "tile"): (891007744 + 2925925632, "d8b350db0c17d40c"),
 }
 
 
