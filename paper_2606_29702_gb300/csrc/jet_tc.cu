@@ -75,8 +75,8 @@ constexpr double kSliceBudgetBytes = 48.0 * 1024 * 1024;
 // Wbar^l = sum over the tiles of a K range of Zbar^l A^{l-1}^T, both operands
 // read from the store in the fused kernel's swizzled layout, 64 columns
 // (one layout chunk) per pipeline stage; the accumulator stays in TMEM for
-// the whole range and is written once to the item's partial, in FP32 (its own
-// precision: the FP64 sum over the items reads the same values).
+// the whole range and is written once to the item's partial, in FP32 (the
+// accumulator's own precision).
 struct WgArgs {
   const unsigned char* wstore;
   long long tile_stride;  // bytes per tile in the store
@@ -226,30 +226,10 @@ struct OffWl {
   long long v[kMaxLayers];
 };
 
-// (offW is a __grid_constant__: read in place, not copied to local memory for the runtime index)
-__global__ void wgrad_sum_kernel(const float* out, int L, int w, int wu, int G, int ipl,
-                                 const __grid_constant__ OffWl offW, double* dst) {
-  const long long ww = (long long)w * w, uu = (long long)wu * wu, total = (long long)(L - 2) * uu;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int li = (int)(e / uu);
-    const long long r = e % uu;
-    const int i = (int)(r / wu), k = (int)(r % wu);
-    const float* src = out + (long long)li * ipl * ww;
-    double s = 0.0;
-    for (int b = 0; b < G; ++b) {
-      const long long o = (long long)(b * wu + i) * w + b * wu + k;
-      // the item partials in a fixed order; the loads of eight items issue together
-#pragma unroll 8
-      for (int it = 0; it < ipl; ++it) s += (double)src[it * ww + o];
-    }
-    dst[offW.v[li + 1] + r] += s;
-  }
-}
-
-// The same sum, four consecutive elements of a row per thread (wu % 4 == 0):
-// 16-byte loads; each element's items in the same order as above, eight at
-// a time in FP32 before each FP64 add.
+// Four consecutive elements of a row per thread (hidden widths are multiples
+// of 32), 16-byte loads; each element's items in item order, eight at a time
+// in FP32 before each FP64 add.  offW is a __grid_constant__: read in place,
+// not copied to local memory for its runtime index.
 __global__ void wgrad_sum4_kernel(const float* out, int L, int w, int wu, int G, int ipl,
                                   const __grid_constant__ OffWl offW, double* dst) {
   const long long ww = (long long)w * w, uu = (long long)wu * wu, total4 = (long long)(L - 2) * uu / 4;
@@ -933,12 +913,8 @@ jet_status run(jet_plan_s* p, TcPlan* t, int mode, const TcInst& I, cudaStream_t
       OffWl ow;
       for (int l = 0; l < L; ++l) ow.v[l] = p->off_W[l];
       const long long tot = (long long)(L - 2) * t->wu * t->wu;
-      if (t->wu % 4 == 0)
-        wgrad_sum4_kernel<<<(int)std::min<long long>((tot / 4 + 255) / 256, 2048), 256, 0, s>>>(
-            t->wg_out, L, t->w, t->wu, t->G, w.items_per_layer, ow, t->grad_slices);
-      else
-        wgrad_sum_kernel<<<(int)std::min<long long>((tot + 255) / 256, 2048), 256, 0, s>>>(
-            t->wg_out, L, t->w, t->wu, t->G, w.items_per_layer, ow, t->grad_slices);
+      wgrad_sum4_kernel<<<(int)std::min<long long>((tot / 4 + 255) / 256, 2048), 256, 0, s>>>(
+          t->wg_out, L, t->w, t->wu, t->G, w.items_per_layer, ow, t->grad_slices);
       e = cudaGetLastError();
     }
   }
